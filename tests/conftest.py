@@ -1,0 +1,18 @@
+"""Shared test configuration.
+
+``gpu`` tests need a CUDA device (GB300) and the compiled library; everything
+else runs on the CPU.
+"""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled library")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds")
