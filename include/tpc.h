@@ -1,0 +1,162 @@
+/*
+ * tpc — GB300 (sm_103a) clustering of Timepix hits into connected components.
+ *
+ * C ABI of the CUDA library libtpc.so.  The problem is the one of
+ * Celko, Mraz, Bergmann, Manek, "Parallel CPU- and GPU-based connected
+ * component algorithms for event building for hybrid pixel detectors"
+ * (arXiv:2412.11809), Section 2: group zero-suppressed hits (x, y, ToA, ToT)
+ * into clusters that are maximal (i), spatially 8-connected (ii) and satisfy a
+ * temporal condition (iii):
+ *   TPC_LOCAL  (iii)(a)  every step of a connecting path has |dToA| <= dt;
+ *   TPC_GLOBAL (iii)(b)  every hit but the first has a cluster hit <= dt earlier;
+ *   TPC_STATIC (iii)(c)  all ToAs of a cluster lie within dt.
+ * A pixel counts as its own neighbour (Section 4.1: "the 8 neighbouring pixels
+ * plus the pixel itself"); ToA comparisons are inclusive.  (b) and (c) are
+ * evaluated as the time sweep of Algorithm 1 in (ToA, index) order: a hit
+ * merges every still-open cluster with a member on one of its 9 pixels;
+ * (b) open = last ToA >= toa - dt, (c) open = first ToA >= toa - dt.
+ *
+ * Conventions for every call:
+ *   - All functions return 0 (TPC_OK) or a negative tpc_status; no call
+ *     throws, aborts or traps.  tpc_strerror() names a status.
+ *   - Hit indices are global stream indices: 0-based positions in the order
+ *     of all tpc_push() calls on a context.
+ *   - A label is the smallest global index in its cluster (canonical).
+ *   - `where` says whether a pointer is host (TPC_HOST) or device
+ *     (TPC_DEVICE, memory of the context's CUDA device) memory.
+ *   - The caller owns every buffer it passes.  The library owns all device
+ *     state it allocates and frees it in tpc_destroy().
+ *   - Work is ordered on the context's CUDA stream (TPC_OPT_STREAM).  A
+ *     context must not be used from two host threads at once; different
+ *     contexts are independent and may run concurrently.
+ */
+#ifndef TPC_H
+#define TPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One hit, 16 bytes, little endian.  ToA in 1.5625 ns ticks. */
+typedef struct tpc_hit {
+    uint16_t x;         /* column, < width */
+    uint16_t y;         /* row, < height */
+    uint16_t tot;       /* time over threshold (weight of the centroid) */
+    uint16_t reserved;  /* ignored */
+    uint64_t toa;       /* time of arrival */
+} tpc_hit;
+
+/* One cluster record, 40 bytes. */
+typedef struct tpc_cluster {
+    uint64_t label;     /* smallest global hit index in the cluster */
+    int64_t size;       /* number of hits */
+    int64_t sum_tot;    /* sum of ToT, exact */
+    uint64_t first_toa; /* smallest ToA */
+    float cx, cy;       /* ToT-weighted centroid sum(tot*x)/sum(tot), integer
+                           pixel coordinates, from exact integer sums rounded
+                           once to fp32; NaN when sum_tot == 0 */
+} tpc_cluster;
+
+typedef enum {
+    TPC_OK = 0,
+    TPC_ERR_ARG = -1,     /* null pointer, bad variant/key/where, sensor too large */
+    TPC_ERR_RANGE = -2,   /* a hit with x >= width or y >= height (found on device) */
+    TPC_ERR_NOMEM = -3,   /* device or pinned allocation failed */
+    TPC_ERR_BUSY = -4,    /* admission refused: the memory budget would be exceeded */
+    TPC_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up */
+    TPC_ERR_CUDA = -6,    /* a CUDA runtime call failed */
+    TPC_ERR_CAP = -7,     /* output buffer too small; *n_out holds the size needed */
+    TPC_ERR_SPAN = -8,    /* ToA span of one processing step is >= 2^32 ticks */
+    TPC_ERR_LATE = -9,    /* streaming: a hit arrived later than max_disorder allows */
+    TPC_ERR_STATE = -10   /* call not valid in the context's current state */
+} tpc_status;
+
+typedef enum { TPC_LOCAL = 0, TPC_GLOBAL = 1, TPC_STATIC = 2 } tpc_variant;
+typedef enum { TPC_HOST = 0, TPC_DEVICE = 1 } tpc_where;
+
+typedef enum {
+    /* Streaming (Algorithm 2's t, Section 3.1's t-ordered streams): the
+       largest amount by which a later hit may precede an earlier one.  When
+       set (< UINT64_MAX), every tpc_push() clusters the new chunk together
+       with the open clusters carried on the device and finalises every
+       cluster whose last ToA <= max_toa_seen - max_disorder - dt.  Default
+       UINT64_MAX: pushes only buffer, tpc_flush() clusters everything. */
+    TPC_OPT_MAX_DISORDER = 1,
+    /* Device-memory budget in bytes for this context's working set; a push
+       that would exceed it fails with TPC_ERR_BUSY and changes nothing.
+       Default 0 = unlimited. */
+    TPC_OPT_MEM_BUDGET = 2,
+    /* cudaStream_t (cast to uint64_t) on which all work is ordered.
+       Default 0 = a stream the context creates. */
+    TPC_OPT_STREAM = 3,
+    /* CTAs per SM for the persistent kernels (0 = default / autotuned). */
+    TPC_OPT_CTAS_PER_SM = 4
+} tpc_option;
+
+typedef struct tpc_ctx tpc_ctx;
+
+/* Create a context for one sensor of width x height pixels (width*height <=
+   2^20) with time window dt (ticks) and a variant.  Uses the current CUDA
+   device.  *out receives the context; on error *out is NULL. */
+int tpc_create(uint32_t width, uint32_t height, uint64_t dt, int variant, tpc_ctx **out);
+
+/* Set an option (see tpc_option).  Options may change only while no hits
+   are pending (TPC_ERR_STATE otherwise). */
+int tpc_set_option(tpc_ctx *ctx, int key, uint64_t value);
+
+/* Append n hits (a chunk) to the stream.  Host hits are copied (through a
+   pinned staging buffer) before the call returns.  Device hits are read by
+   work queued on the context stream: the caller must keep them unchanged
+   until tpc_sync() (or a retrieval call) returns.  In streaming mode the
+   chunk is clustered at once; otherwise it is buffered for tpc_flush(). */
+int tpc_push(tpc_ctx *ctx, const tpc_hit *hits, size_t n, int where);
+
+/* Cluster everything pending and close every cluster (the end of the
+   stream).  Asynchronous: errors found on the device are reported by
+   tpc_sync() and the retrieval calls. */
+int tpc_flush(tpc_ctx *ctx);
+
+/* Wait for the context's queued work; returns the first device-side error
+   of the last processing step, if any. */
+int tpc_sync(tpc_ctx *ctx);
+
+/* Labels of the hits finalised by the last processing step (the last push
+   in streaming mode, or tpc_flush), in increasing global index.  After a
+   plain push...push, flush these are all hits.  labels[k] is the label of
+   global hit indices[k]; `indices` may be NULL.  Both buffers hold at least
+   cap entries and live in `where` memory.  *n_out = number of hits
+   finalised; if it exceeds cap, nothing is written and TPC_ERR_CAP is
+   returned. */
+int tpc_labels(tpc_ctx *ctx, uint64_t *labels, uint64_t *indices, size_t cap,
+               size_t *n_out, int where);
+
+/* Cluster records finalised by the last processing step, ordered by label.
+   Same size protocol as tpc_labels. */
+int tpc_cluster_features(tpc_ctx *ctx, tpc_cluster *out, size_t cap, size_t *n_out,
+                         int where);
+
+/* Cluster the pending hits of n contexts in one batch: every kernel of the
+   pipeline runs once over all contexts (persistent CTAs over (context, tile)
+   work items), replayed from one CUDA graph.  All contexts must be on the
+   same device, non-streaming, with pending hits pushed; results are read
+   per context with tpc_labels / tpc_cluster_features.  Work is ordered on the
+   first context's stream; every context's stream waits for it. */
+int tpc_batch_flush(tpc_ctx **ctxs, int n);
+
+/* Number of hits finalised, clusters finalised and hits carried (open) by
+   the last processing step.  Waits for the context's work. */
+int tpc_counts(tpc_ctx *ctx, size_t *n_hits, size_t *n_clusters, size_t *n_open);
+
+/* Bytes of device memory the context currently holds. */
+int tpc_device_bytes(tpc_ctx *ctx, size_t *bytes);
+
+const char *tpc_strerror(int status);
+void tpc_destroy(tpc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPC_H */

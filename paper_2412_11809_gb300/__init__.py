@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) clustering of Timepix hits into connected components.
+
+The compute lives in the CUDA library ``_build/libtpc.so`` (C ABI in
+``include/tpc.h``); this package is its binding.  See ``Clusterer``.
+"""
+from .binding import (CLUSTER_DTYPE, HIT_DTYPE, Clusterer, TpcError, batch_flush,
+                      load_library)
+
+__all__ = ["CLUSTER_DTYPE", "HIT_DTYPE", "Clusterer", "TpcError", "batch_flush", "load_library"]

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libtpc (the C ABI declared in include/tpc.h).
+
+Argument marshalling only: every step of the clustering runs in the CUDA
+library.  There is no CPU fallback — if libtpc.so is missing the import of a
+Clusterer fails loudly.  Device memory and streams come from PyTorch when
+device tensors are passed; host data are numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HIT_DTYPE = np.dtype([("x", "<u2"), ("y", "<u2"), ("tot", "<u2"),
+                      ("reserved", "<u2"), ("toa", "<u8")])
+CLUSTER_DTYPE = np.dtype([("label", "<u8"), ("size", "<i8"), ("sum_tot", "<i8"),
+                          ("first_toa", "<u8"), ("cx", "<f4"), ("cy", "<f4")])
+assert HIT_DTYPE.itemsize == 16 and CLUSTER_DTYPE.itemsize == 40
+
+TPC_HOST, TPC_DEVICE = 0, 1
+VARIANTS = {"local": 0, "global": 1, "static": 2, 0: 0, 1: 1, 2: 2}
+OPT_MAX_DISORDER, OPT_MEM_BUDGET, OPT_STREAM, OPT_CTAS_PER_SM = 1, 2, 3, 4
+
+STATUS = {0: "TPC_OK", -1: "TPC_ERR_ARG", -2: "TPC_ERR_RANGE", -3: "TPC_ERR_NOMEM",
+          -4: "TPC_ERR_BUSY", -5: "TPC_ERR_TIMEOUT", -6: "TPC_ERR_CUDA", -7: "TPC_ERR_CAP",
+          -8: "TPC_ERR_SPAN", -9: "TPC_ERR_LATE", -10: "TPC_ERR_STATE"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libtpc.so")
+
+# every entry point of include/tpc.h with its ctypes signature
+_VP, _SZ, _U64, _U32, _INT = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+SIGNATURES = {
+    "tpc_create": ([_U32, _U32, _U64, _INT, ctypes.POINTER(_VP)], _INT),
+    "tpc_set_option": ([_VP, _INT, _U64], _INT),
+    "tpc_push": ([_VP, _VP, _SZ, _INT], _INT),
+    "tpc_flush": ([_VP], _INT),
+    "tpc_sync": ([_VP], _INT),
+    "tpc_labels": ([_VP, _VP, _VP, _SZ, ctypes.POINTER(_SZ), _INT], _INT),
+    "tpc_cluster_features": ([_VP, _VP, _SZ, ctypes.POINTER(_SZ), _INT], _INT),
+    "tpc_batch_flush": ([ctypes.POINTER(_VP), _INT], _INT),
+    "tpc_counts": ([_VP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)], _INT),
+    "tpc_device_bytes": ([_VP, ctypes.POINTER(_SZ)], _INT),
+    "tpc_strerror": ([_INT], ctypes.c_char_p),
+    "tpc_destroy": ([_VP], None),
+}
+
+_lib = None
+
+
+class TpcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        msg = _lib.tpc_strerror(status).decode() if _lib is not None else self.name
+        super().__init__(f"{what}: {self.name} ({msg})" if what else f"{self.name} ({msg})")
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtpc.so and declare its signatures.  Raises if it is not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtpc.so not found at {path}: build it with "
+                               "paper_2412_11809_gb300.build.build() (needs nvcc)")
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise TpcError(rc, what)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _device_hits(t):
+    """(pointer, n) of a contiguous CUDA tensor holding 16-byte hit records."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device hits must be a contiguous CUDA tensor")
+    nbytes = t.numel() * t.element_size()
+    if nbytes % 16:
+        raise ValueError("device hits must hold whole 16-byte records")
+    return t.data_ptr(), nbytes // 16
+
+
+class Clusterer:
+    """One clustering context (one sensor / stream), see ``tpc_create``."""
+
+    def __init__(self, width: int, height: int, dt: int, variant="local", *,
+                 max_disorder: int | None = None, mem_budget: int | None = None,
+                 stream=None, ctas_per_sm: int | None = None):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.tpc_create(width, height, dt, VARIANTS[variant], ctypes.byref(h)), "tpc_create")
+        self._h = h
+        self._lib = lib
+        self._keep = []          # device inputs that must outlive the queued work
+        self._own_stream = stream is None
+        self.width, self.height, self.dt = width, height, dt
+        if stream is not None:
+            raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            _check(lib.tpc_set_option(h, OPT_STREAM, raw), "stream")
+        if mem_budget is not None:
+            _check(lib.tpc_set_option(h, OPT_MEM_BUDGET, mem_budget), "mem_budget")
+        if ctas_per_sm is not None:
+            _check(lib.tpc_set_option(h, OPT_CTAS_PER_SM, ctas_per_sm), "ctas_per_sm")
+        if max_disorder is not None:
+            _check(lib.tpc_set_option(h, OPT_MAX_DISORDER, max_disorder), "max_disorder")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def push(self, hits):
+        """Append a chunk: a numpy array of HIT_DTYPE (host) or a CUDA tensor."""
+        if _is_torch(hits):
+            ptr, n = _device_hits(hits)
+            self._keep.append(hits)
+            if self._own_stream:
+                # the context's stream does not order after torch's: let the
+                # producer of `hits` finish first
+                import torch
+                torch.cuda.current_stream(hits.device).synchronize()
+            _check(self._lib.tpc_push(self._h, ptr, n, TPC_DEVICE), "tpc_push")
+        else:
+            a = np.ascontiguousarray(hits)
+            if a.dtype != HIT_DTYPE:
+                raise TypeError(f"host hits must have dtype {HIT_DTYPE}")
+            _check(self._lib.tpc_push(self._h, a.ctypes.data if len(a) else None, len(a), TPC_HOST),
+                   "tpc_push")
+
+    def flush(self):
+        _check(self._lib.tpc_flush(self._h), "tpc_flush")
+
+    def sync(self):
+        rc = self._lib.tpc_sync(self._h)
+        self._keep.clear()
+        _check(rc, "tpc_sync")
+
+    def counts(self) -> tuple[int, int, int]:
+        a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self._lib.tpc_counts(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "tpc_counts")
+        return a.value, b.value, c.value
+
+    def labels(self, device: bool = False, with_indices: bool = False):
+        """Labels finalised by the last step (uint64 numpy, or int64 CUDA tensor)."""
+        n, _, _ = self.counts()
+        n_out = ctypes.c_size_t()
+        if device:
+            import torch
+            lab = torch.empty(n, dtype=torch.int64, device="cuda")
+            idx = torch.empty(n, dtype=torch.int64, device="cuda") if with_indices else None
+            _check(self._lib.tpc_labels(self._h, lab.data_ptr() if n else None,
+                                        idx.data_ptr() if (idx is not None and n) else None,
+                                        n, ctypes.byref(n_out), TPC_DEVICE), "tpc_labels")
+        else:
+            lab = np.empty(n, dtype=np.uint64)
+            idx = np.empty(n, dtype=np.uint64) if with_indices else None
+            _check(self._lib.tpc_labels(self._h, lab.ctypes.data if n else None,
+                                        idx.ctypes.data if (idx is not None and n) else None,
+                                        n, ctypes.byref(n_out), TPC_HOST), "tpc_labels")
+        self._keep.clear()
+        return (lab, idx) if with_indices else lab
+
+    def features(self, device: bool = False):
+        """Cluster records finalised by the last step, ordered by label."""
+        _, m, _ = self.counts()
+        n_out = ctypes.c_size_t()
+        if device:
+            import torch
+            rec = torch.empty((m, CLUSTER_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+            _check(self._lib.tpc_cluster_features(self._h, rec.data_ptr() if m else None, m,
+                                                  ctypes.byref(n_out), TPC_DEVICE), "features")
+        else:
+            rec = np.empty(m, dtype=CLUSTER_DTYPE)
+            _check(self._lib.tpc_cluster_features(self._h, rec.ctypes.data if m else None, m,
+                                                  ctypes.byref(n_out), TPC_HOST), "features")
+        return rec
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(self._lib.tpc_device_bytes(self._h, ctypes.byref(b)), "tpc_device_bytes")
+        return b.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tpc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def batch_flush(clusterers) -> None:
+    """Cluster the pending hits of several contexts in one batched step."""
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(clusterers))(*[c.handle.value for c in clusterers])
+    _check(lib.tpc_batch_flush(arr, len(clusterers)), "tpc_batch_flush")

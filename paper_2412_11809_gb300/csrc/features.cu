@@ -1,0 +1,287 @@
+// Per-cluster features, canonical labels and stream compaction.
+//
+// k_accumulate walks the hits in input order (16-byte coalesced loads) and
+// reduces size, sum ToT, sum ToT*x, sum ToT*y, smallest position and largest
+// key into the root's slot.  Hits of one cluster that share a warp are
+// combined first (match.any + redux.sync), so one lane per cluster and warp
+// issues the atomics.  Integer sums are exact; the centroid is one division
+// of exact sums (features are the purpose named in Section 1: on-the-fly
+// filtering and compression; Algorithm 3 step 6 orders clusters by time,
+// here records are ordered by label instead).
+//
+// k_labels writes label = global index of the smallest position of the
+// cluster and sets two bit flags per position (label hit of a finalised
+// cluster; hit of a finalised cluster) with one ballot per warp.
+// k_tile_scan turns per-tile flag counts into per-segment offsets;
+// k_records and k_stream_compact write the compacted outputs and, when
+// streaming, the carry of open hits for the next step.
+#include "tpc_internal.cuh"
+
+namespace tpc {
+
+__device__ __forceinline__ uint32_t lanemask_lt_f() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Sum of a 32-bit value over `peers` without overflow (< 2^32 each, <= 32 lanes).
+__device__ __forceinline__ unsigned long long reduce_add_wide(uint32_t peers, uint32_t v) {
+    const uint32_t hi = __reduce_add_sync(peers, v >> 16);
+    const uint32_t lo = __reduce_add_sync(peers, v & 0xFFFFu);
+    return ((unsigned long long)hi << 16) + lo;
+}
+
+__global__ void __launch_bounds__(256) k_accumulate(Work w) {
+    const uint32_t nt = w.prob->ntiles;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint64_t base = g.toa_min;
+        for (uint32_t p0 = begin; p0 < end; p0 += blockDim.x) {
+            const uint32_t pos = p0 + threadIdx.x;
+            const bool valid = pos < end;
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+            if (!valid) continue;
+            const uint32_t r = w.root_of[pos];
+            const uint4 v = ld_hit(g.hits + (pos - g.off));
+            const uint32_t tot = hit_tot(v), x = hit_x(v), y = hit_y(v);
+            const uint32_t key = (uint32_t)(hit_toa(v) - base);
+            const uint32_t peers = __match_any_sync(vmask, r);
+            const uint32_t sum_tot = __reduce_add_sync(peers, tot);
+            const unsigned long long wx = reduce_add_wide(peers, tot * x);
+            const unsigned long long wy = reduce_add_wide(peers, tot * y);
+            const uint32_t mn = __reduce_min_sync(peers, pos);
+            const uint32_t mx = __reduce_max_sync(peers, key);
+            if (lane == __ffs(peers) - 1) {
+                atomicAdd(&w.slot_size[r], (uint32_t)__popc(peers));
+                atomicAdd(&w.slot_tot[r], (unsigned long long)sum_tot);
+                atomicAdd(&w.slot_wx[r], wx);
+                atomicAdd(&w.slot_wy[r], wy);
+                atomicMin(&w.slot_min[r], mn);
+                atomicMax(&w.slot_maxkey[r], mx);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ bool cluster_closed(const Seg &g, uint32_t maxkey) {
+    if (g.close_mode == CLOSE_ALL) return true;
+    if (g.close_mode == CLOSE_NONE) return false;
+    return g.toa_min + (uint64_t)maxkey <= g.watermark;
+}
+
+__global__ void __launch_bounds__(256) k_labels(Work w) {
+    __shared__ uint32_t s_cnt[2];
+    const uint32_t nt = w.prob->ntiles;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const bool direct = g.ss == nullptr;   // one-shot: every hit is final
+        if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        uint32_t c_label = 0, c_closed = 0;
+        for (uint32_t p0 = begin; p0 < end; p0 += blockDim.x) {
+            const uint32_t pos = p0 + threadIdx.x;
+            const bool valid = pos < end;
+            bool is_label = false, closed = false;
+            if (valid) {
+                const uint32_t r = w.root_of[pos];
+                const uint32_t l = w.slot_min[r];
+                closed = cluster_closed(g, w.slot_maxkey[r]);
+                is_label = closed && l == pos;
+                const uint64_t lab = gidx_of(g, l - g.off);
+                if (direct) g.out_labels[pos - g.off] = lab;
+                else w.lab_tmp[pos] = lab;
+            }
+            const uint32_t bl = __ballot_sync(0xffffffffu, is_label);
+            const uint32_t bc = __ballot_sync(0xffffffffu, valid && closed);
+            if (lane == 0) {
+                w.flag_label[pos >> 5] = bl;
+                w.flag_closed[pos >> 5] = bc;
+                c_label += __popc(bl);
+                c_closed += __popc(bc);
+            }
+        }
+        if (lane == 0) {
+            atomicAdd(&s_cnt[0], c_label);
+            atomicAdd(&s_cnt[1], c_closed);
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) w.tile_cnt[threadIdx.x * w.prob->tile_cap + t] = s_cnt[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// One CTA per segment: exclusive scans of the tile counts; totals.
+__global__ void __launch_bounds__(1024) k_tile_scan(Work w) {
+    __shared__ uint32_t s_warp[32];
+    const uint32_t s = blockIdx.x;
+    if (s >= w.prob->nsegs) return;
+    Seg &g = w.seg[s];
+    const uint32_t cap = w.prob->tile_cap;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int kind = 0; kind < 2; ++kind) {
+        uint32_t running = 0;
+        for (uint32_t c = 0; c < g.ntiles; c += blockDim.x) {
+            const uint32_t t = g.tile0 + c + threadIdx.x;
+            const bool valid = c + threadIdx.x < g.ntiles;
+            const uint32_t v = valid ? w.tile_cnt[kind * cap + t] : 0;
+            uint32_t x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_warp[warp] = x;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t q = s_warp[lane];
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(0xffffffffu, q, o);
+                    if (lane >= o) q += y;
+                }
+                s_warp[lane] = q;
+            }
+            __syncthreads();
+            const uint32_t ex = (warp ? s_warp[warp - 1] : 0) + x - v;
+            if (valid) w.tile_base[kind * cap + t] = running + ex;
+            running += s_warp[31];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (kind == 0) g.n_clusters = running;
+            else { g.n_final = running; g.n_open = g.n - running; }
+        }
+    }
+    if (threadIdx.x == 0 && g.n_clusters > g.out_cap) atomicOr(&w.prob->err, E_CAP);
+}
+
+// One thread per flag word (TILE / 32 = 128 words per tile).
+__global__ void __launch_bounds__(TILE_WORDS) k_records(Work w) {
+    __shared__ uint32_t s_warp[TILE_WORDS / 32];
+    const uint32_t nt = w.prob->ntiles, cap = w.prob->tile_cap;
+    const uint32_t *skey = w.keys[sorted_sel(*w.prob)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t nwords = (end - begin + 31) >> 5;
+        uint32_t bits = threadIdx.x < nwords ? w.flag_label[(begin >> 5) + threadIdx.x] : 0;
+        const uint32_t c = __popc(bits);
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int q = 0; q < warp; ++q) wpre += s_warp[q];
+        uint32_t ord = w.tile_base[t] + wpre + x - c;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const uint32_t pos = begin + (threadIdx.x << 5) + b;
+            const uint32_t r = w.root_of[pos];
+            if (ord < g.out_cap) {
+                tpc_cluster rec;
+                rec.label = gidx_of(g, pos - g.off);
+                rec.size = (int64_t)w.slot_size[r];
+                rec.sum_tot = (int64_t)w.slot_tot[r];
+                rec.first_toa = g.toa_min + skey[r];
+                const double sw = (double)w.slot_tot[r];
+                rec.cx = (float)((double)w.slot_wx[r] / sw);
+                rec.cy = (float)((double)w.slot_wy[r] / sw);
+                g.out_rec[ord] = rec;
+            }
+            ++ord;
+        }
+        __syncthreads();
+    }
+    (void)cap;
+}
+
+// Streaming: finalised hits -> (label, index) in increasing global index;
+// open hits -> the next step's carry, right aligned in its carry region.
+__global__ void __launch_bounds__(TILE_WORDS) k_stream_compact(Work w) {
+    __shared__ uint32_t s_warp[TILE_WORDS / 32];
+    const uint32_t nt = w.prob->ntiles, cap = w.prob->tile_cap;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        if (!g.ss) continue;
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t nwords = (end - begin + 31) >> 5;
+        const bool vw = threadIdx.x < nwords;
+        const uint32_t bits = vw ? w.flag_closed[(begin >> 5) + threadIdx.x] : 0;
+        const uint32_t c = __popc(bits);
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int q = 0; q < warp; ++q) wpre += s_warp[q];
+        const uint32_t closed_before = w.tile_base[cap + t] + wpre + x - c;
+        const bool carry_fits = g.n_open <= g.carry_cap;
+        if (!carry_fits && threadIdx.x == 0) atomicOr(&w.prob->err, E_CAP);
+        if (vw) {
+            const uint32_t first = begin + (threadIdx.x << 5);
+            const uint32_t last = first + 32 < end ? first + 32 : end;
+            uint32_t k_closed = 0;
+            for (uint32_t pos = first; pos < last; ++pos) {
+                const uint32_t local = pos - g.off;
+                const bool cl = (bits >> (pos - first)) & 1u;
+                if (cl) {
+                    const uint32_t ord = closed_before + k_closed++;
+                    if (ord < g.out_cap) {
+                        g.out_labels[ord] = w.lab_tmp[pos];
+                        if (g.out_index) g.out_index[ord] = gidx_of(g, local);
+                    }
+                } else if (carry_fits) {
+                    const uint32_t open_rank = local - (closed_before + k_closed);
+                    const uint32_t dst = g.carry_cap - g.n_open + open_rank;
+                    g.carry_out[dst] = g.hits[local];
+                    g.carry_gidx_out[dst] = gidx_of(g, local);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_stream_end(Work w) {
+    const uint32_t nsegs = w.prob->nsegs;
+    for (uint32_t s = threadIdx.x; s < nsegs; s += blockDim.x) {
+        Seg &g = w.seg[s];
+        if (!g.ss) continue;
+        StreamState &ss = *g.ss;
+        if (g.n_open > g.carry_cap) atomicOr(&w.prob->err, E_CAP);
+        ss.n_carry = g.n_open <= g.carry_cap ? g.n_open : 0;
+        ss.seen_max = g.seen_after;
+        ss.has_seen = ss.has_seen || g.n != 0;
+        if (g.close_mode == CLOSE_WM) ss.watermark = g.watermark;
+    }
+}
+
+void launch_features(const Work &w, const Launch &L) {
+    k_accumulate<<<L.grid, 256, 0, L.stream>>>(w);
+}
+
+void launch_outputs(const Work &w, const Launch &L) {
+    k_labels<<<L.grid, 256, 0, L.stream>>>(w);
+    k_tile_scan<<<MAX_SEGS, 1024, 0, L.stream>>>(w);
+    k_records<<<L.grid, TILE_WORDS, 0, L.stream>>>(w);
+    k_stream_compact<<<L.grid, TILE_WORDS, 0, L.stream>>>(w);
+    k_stream_end<<<1, 256, 0, L.stream>>>(w);
+}
+
+}  // namespace tpc

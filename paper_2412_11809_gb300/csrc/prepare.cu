@@ -1,0 +1,217 @@
+// Step set-up, coalesced 16-byte hit loads with range validation and ToA
+// min/max (Algorithm 3, steps 1-2: the hits arrive on the device), sort keys,
+// and the post-sort gather of pixel coordinates.
+#include "tpc_internal.cuh"
+
+namespace tpc {
+
+// One CTA: lay the segments out in position space, reset per-step state and
+// fill the tile -> segment table.  Streaming segments pick up the carry left
+// by the previous step: it sits right-aligned in the carry region of their
+// input buffer, immediately followed by the new chunk.
+__global__ void k_setup(Work w, int nsegs) {
+    __shared__ uint32_t s_tile0[MAX_SEGS + 1];
+    if (threadIdx.x == 0) {
+        uint32_t off = 0, tile = 0;
+        for (int s = 0; s < nsegs; ++s) {
+            Seg &g = w.seg[s];
+            if (g.ss) {
+                g.n_carry = g.ss->n_carry;
+                g.hits = g.carry_in + (g.carry_cap - g.n_carry);
+                g.carry_gidx = g.carry_gidx_in + (g.carry_cap - g.n_carry);
+            } else {
+                g.n_carry = 0;
+                g.carry_gidx = nullptr;
+            }
+            g.n = g.n_carry + g.n_new;
+            g.off = off;
+            g.tile0 = tile;
+            g.ntiles = (g.n + TILE - 1) / TILE;
+            off += g.ntiles * TILE;
+            tile += g.ntiles;
+            g.toa_min = ~0ull;
+            g.toa_max = 0;
+            g.chunk_min = ~0ull;
+            g.npasses = 0;
+            g.watermark = 0;
+            g.close_mode = CLOSE_NONE;
+            g.seen_after = 0;
+            g.n_final = g.n_clusters = g.n_open = 0;
+            s_tile0[s] = g.tile0;
+        }
+        s_tile0[nsegs] = tile;
+        Prob &p = *w.prob;
+        p.nsegs = (uint32_t)nsegs;
+        p.npasses = 0;
+        p.err = 0;
+        p.ntiles = tile;
+        if (tile > p.tile_cap || off > p.pos_cap) {
+            p.err |= E_CAP;
+            p.ntiles = 0;
+        }
+    }
+    __syncthreads();
+    const uint32_t nt = w.prob->ntiles;
+    for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) {
+        int lo = 0, hi = nsegs - 1;   // last segment whose first tile <= t
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (s_tile0[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        w.tile_seg[t] = (uint32_t)lo;
+    }
+}
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+    for (int o = 16; o; o >>= 1) {
+        uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+    for (int o = 16; o; o >>= 1) {
+        uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
+// Load every hit once (16-byte vector loads, consecutive threads on
+// consecutive hits), reject hits outside the sensor, reduce ToA min/max.
+__global__ void __launch_bounds__(256) k_prepare(Work w) {
+    __shared__ uint64_t s_red[3][8];
+    const uint32_t nt = w.prob->ntiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const uint32_t si = w.tile_seg[t];
+        const Seg &g = w.seg[si];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const tpc_hit *hits = g.hits;
+        const uint32_t off = g.off, W = g.width, H = g.height, nc = g.n_carry;
+        uint64_t mn = ~0ull, mx = 0, cmn = ~0ull;
+        bool bad = false;
+        for (uint32_t pos = begin + threadIdx.x; pos < end; pos += blockDim.x) {
+            const uint32_t j = pos - off;
+            uint4 v = ld_hit(hits + j);
+            bad |= hit_x(v) >= W || hit_y(v) >= H;
+            uint64_t toa = hit_toa(v);
+            mn = toa < mn ? toa : mn;
+            mx = toa > mx ? toa : mx;
+            if (j >= nc) cmn = toa < cmn ? toa : cmn;
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&w.prob->err, E_RANGE);
+        mn = warp_min_u64(mn);
+        mx = warp_max_u64(mx);
+        cmn = warp_min_u64(cmn);
+        if (lane == 0) { s_red[0][warp] = mn; s_red[1][warp] = mx; s_red[2][warp] = cmn; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+                mn = s_red[0][i] < mn ? s_red[0][i] : mn;
+                mx = s_red[1][i] > mx ? s_red[1][i] : mx;
+                cmn = s_red[2][i] < cmn ? s_red[2][i] : cmn;
+            }
+            Seg &gw = w.seg[si];
+            atomicMin(reinterpret_cast<unsigned long long *>(&gw.toa_min), (unsigned long long)mn);
+            atomicMax(reinterpret_cast<unsigned long long *>(&gw.toa_max), (unsigned long long)mx);
+            atomicMin(reinterpret_cast<unsigned long long *>(&gw.chunk_min), (unsigned long long)cmn);
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA: per-segment radix pass count, ToA span check, and the streaming
+// watermark.  A later hit j satisfies toa_j > seen_max - max_disorder (the
+// t-ordered property, Section 3.1), and can join hit i only if
+// toa_j - toa_i <= dt, so every cluster whose last ToA <=
+// seen_max - max_disorder - dt is final.
+__global__ void k_seg_finalize(Work w) {
+    const uint32_t nsegs = w.prob->nsegs;
+    for (uint32_t s = threadIdx.x; s < nsegs; s += blockDim.x) {
+        Seg &g = w.seg[s];
+        uint32_t passes = 0;
+        if (g.n) {
+            uint64_t span = g.toa_max - g.toa_min;
+            if (span >> 32) {
+                atomicOr(&w.prob->err, E_SPAN);
+            } else if (span) {
+                uint32_t bits = 64 - __clzll((long long)span);
+                passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
+            }
+        }
+        g.npasses = passes;
+        atomicMax(&w.prob->npasses, passes);
+        if (!g.ss) {
+            g.close_mode = CLOSE_ALL;   // one-shot: the end of the stream
+            continue;
+        }
+        StreamState &ss = *g.ss;
+        const uint64_t md = g.max_disorder;   // ~0: a flush of a streaming context
+        if (md != ~0ull && g.n_new && ss.has_seen && ss.seen_max >= md &&
+            g.chunk_min <= ss.seen_max - md)
+            atomicOr(&w.prob->err, E_LATE);
+        uint64_t seen = ss.has_seen ? ss.seen_max : 0;
+        if (g.n && g.toa_max > seen) seen = g.toa_max;
+        g.seen_after = seen;
+        const uint64_t lag = md + (uint64_t)g.dt;
+        if (md == ~0ull) {
+            g.close_mode = CLOSE_ALL;
+        } else if (lag >= md && seen >= lag) {
+            g.close_mode = CLOSE_WM;
+            g.watermark = seen - lag;
+        } else {
+            g.close_mode = CLOSE_NONE;
+        }
+    }
+}
+
+// keys[pos] = ToA - toa_min (32 bits), vals[pos] = pos.
+__global__ void __launch_bounds__(256) k_make_keys(Work w) {
+    const uint32_t nt = w.prob->ntiles;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint64_t base = g.toa_min;
+        for (uint32_t pos = begin + threadIdx.x; pos < end; pos += blockDim.x) {
+            uint4 v = ld_hit(g.hits + (pos - g.off));
+            w.keys[0][pos] = (uint32_t)(hit_toa(v) - base);
+            w.vals[0][pos] = pos;
+        }
+    }
+}
+
+// spix[s] = pixel of the hit at sorted position s.
+__global__ void __launch_bounds__(256) k_gather(Work w) {
+    const uint32_t nt = w.prob->ntiles;
+    const uint32_t *vals = w.vals[sorted_sel(*w.prob)];
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
+            uint4 v = ld_hit(g.hits + (vals[s] - g.off));
+            w.spix[s] = v.x;   // x | y << 16
+        }
+    }
+}
+
+void launch_setup(const Work &w, int nsegs, cudaStream_t st) {
+    k_setup<<<1, 1024, 0, st>>>(w, nsegs);
+}
+void launch_prepare(const Work &w, const Launch &L) {
+    k_prepare<<<L.grid, 256, 0, L.stream>>>(w);
+}
+void launch_seg_finalize(const Work &w, cudaStream_t st) {
+    k_seg_finalize<<<1, 256, 0, st>>>(w);
+}
+void launch_make_keys(const Work &w, const Launch &L) {
+    k_make_keys<<<L.grid, 256, 0, L.stream>>>(w);
+}
+void launch_gather(const Work &w, const Launch &L) {
+    k_gather<<<L.grid, 256, 0, L.stream>>>(w);
+}
+
+}  // namespace tpc

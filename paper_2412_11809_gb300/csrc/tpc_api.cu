@@ -1,0 +1,736 @@
+// C ABI of libtpc: contexts, device memory, the launch sequence of one
+// processing step, streaming carry, batching and CUDA-graph replay.
+//
+// A processing step (tpc_flush, a streaming tpc_push, or tpc_batch_flush)
+// enqueues the same fixed kernel sequence on one CUDA stream:
+//   setup -> prepare (load, validate, ToA min/max) -> finalize -> keys ->
+//   radix passes 0..3 -> gather -> tile link -> border link -> flatten ->
+//   accumulate -> labels -> tile scan -> records -> stream compact -> end.
+// Every size the kernels need is read from device memory and every kernel is
+// a persistent grid over (segment, tile) work items, so no step waits for the
+// host and the sequence is captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "tpc_internal.cuh"
+
+using namespace tpc;
+
+namespace {
+
+constexpr int SEG_RING = 8;
+
+struct DevMem {
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    template <class T>
+    T *alloc(size_t count, cudaError_t &err) {
+        void *p = nullptr;
+        if (err != cudaSuccess) return nullptr;
+        size_t b = std::max<size_t>(count, 1) * sizeof(T);
+        b = (b + 255) & ~size_t(255);
+        err = cudaMalloc(&p, b);
+        if (err != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        bytes += b;
+        return static_cast<T *>(p);
+    }
+    void release() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+        bytes = 0;
+    }
+};
+
+// Device work arrays for up to pos_cap positions in up to seg_cap segments.
+struct Workspace {
+    size_t pos_cap = 0, tile_cap = 0;
+    Work w{};
+    DevMem mem;
+
+    static size_t bytes_for(size_t pos_cap) {
+        const size_t tiles = pos_cap / TILE + MAX_SEGS;
+        return pos_cap * (4 * 4 + 4 * 4 + 3 * 8 + 8 + 2 * 0) + pos_cap / 4 +
+               tiles * (4 + 4 * 4 + RADIX * 4) + MAX_SEGS * (RADIX * 4 + sizeof(Seg)) + (1 << 16);
+    }
+
+    cudaError_t ensure(size_t positions) {
+        size_t need = ((positions + TILE - 1) / TILE) * TILE;
+        if (need <= pos_cap && w.seg) return cudaSuccess;
+        cudaDeviceSynchronize();   // in-flight steps may still use the old arrays
+        mem.release();
+        need = std::max<size_t>(need, TILE);
+        pos_cap = need;
+        tile_cap = need / TILE + MAX_SEGS;   // segments pad to whole tiles
+        const size_t P = pos_cap + (size_t)MAX_SEGS * TILE, T = tile_cap;
+        pos_cap = P;
+        cudaError_t e = cudaSuccess;
+        w.seg = mem.alloc<Seg>(MAX_SEGS, e);
+        w.prob = mem.alloc<Prob>(1, e);
+        w.tile_seg = mem.alloc<uint32_t>(T, e);
+        w.keys[0] = mem.alloc<uint32_t>(P, e);
+        w.keys[1] = mem.alloc<uint32_t>(P, e);
+        w.vals[0] = mem.alloc<uint32_t>(P, e);
+        w.vals[1] = mem.alloc<uint32_t>(P, e);
+        w.spix = mem.alloc<uint32_t>(P, e);
+        w.parent = mem.alloc<uint32_t>(P, e);
+        w.root_of = mem.alloc<uint32_t>(P, e);
+        w.slot_size = mem.alloc<uint32_t>(P, e);
+        w.slot_min = mem.alloc<uint32_t>(P, e);
+        w.slot_maxkey = mem.alloc<uint32_t>(P, e);
+        w.slot_tot = mem.alloc<unsigned long long>(P, e);
+        w.slot_wx = mem.alloc<unsigned long long>(P, e);
+        w.slot_wy = mem.alloc<unsigned long long>(P, e);
+        w.lab_tmp = mem.alloc<uint64_t>(P, e);
+        w.flag_label = mem.alloc<uint32_t>(P / 32 + 1, e);
+        w.flag_closed = mem.alloc<uint32_t>(P / 32 + 1, e);
+        w.tile_cnt = mem.alloc<uint32_t>(2 * T, e);
+        w.tile_base = mem.alloc<uint32_t>(2 * T, e);
+        w.hist = mem.alloc<uint32_t>((size_t)RADIX * T, e);
+        w.segtot = mem.alloc<uint32_t>((size_t)MAX_SEGS * RADIX, e);
+        if (e == cudaSuccess) {
+            Prob p{};
+            p.tile_cap = (uint32_t)T;
+            p.pos_cap = (uint32_t)P;
+            e = cudaMemcpy(w.prob, &p, sizeof(Prob), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            mem.release();
+            w = Work{};
+            pos_cap = tile_cap = 0;
+        }
+        return e;
+    }
+};
+
+int num_sms(int dev) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+int map_err(uint32_t bits) {
+    if (bits & E_RANGE) return TPC_ERR_RANGE;
+    if (bits & E_SPAN) return TPC_ERR_SPAN;
+    if (bits & E_TIMEOUT) return TPC_ERR_TIMEOUT;
+    if (bits & E_CAP) return TPC_ERR_NOMEM;
+    if (bits & E_LATE) return TPC_ERR_LATE;
+    return TPC_OK;
+}
+
+__global__ void k_iota_u64(uint64_t *out, uint64_t base, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = base + i;
+}
+
+}  // namespace
+
+struct tpc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint32_t width = 0, height = 0, dt32 = 0;
+    uint64_t dt = 0;
+    int variant = 0;
+    uint64_t max_disorder = ~0ull;
+    uint64_t budget = 0;
+    int ctas_per_sm = 0;
+    int sms = 1;
+
+    // non-streaming pending hits
+    const tpc_hit *zc = nullptr;   // zero-copy: one device push
+    size_t pending = 0;
+    tpc_hit *in = nullptr;         // materialised pending hits
+    size_t in_cap = 0;
+    uint64_t pushed = 0;           // global index of the next pushed hit
+    uint64_t base = 0;             // global index of the first pending hit
+
+    // streaming buffers: [carry_cap | chunk_cap] each, double buffered
+    tpc_hit *sbuf[2] = {nullptr, nullptr};
+    uint64_t *sgidx[2] = {nullptr, nullptr};
+    size_t carry_cap = 0, chunk_cap = 0;
+    int scur = 1;
+    size_t carry_ub = 0;           // upper bound on the device-side carry count
+    StreamState *ss = nullptr;
+
+    Workspace ws;
+    DevMem outmem;                 // output buffers
+    uint64_t *d_labels = nullptr, *d_index = nullptr;
+    tpc_cluster *d_rec = nullptr;
+    size_t out_cap = 0;
+
+    // where the last step's results live (own workspace or a batch's)
+    Seg *res_seg = nullptr;
+    Prob *res_prob = nullptr;
+    bool has_result = false;
+    bool res_streaming = false;
+    uint64_t res_base = 0;
+
+    // pinned staging
+    Seg *h_seg = nullptr;          // SEG_RING * MAX_SEGS
+    cudaEvent_t seg_ev[SEG_RING] = {};
+    int seg_slot = 0;
+    tpc_hit *h_stage = nullptr;
+    size_t stage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;
+    cudaEvent_t done_ev = nullptr;
+
+    // graph of the step sequence
+    cudaGraphExec_t graph = nullptr;
+    int graph_nsegs = 0;
+    size_t graph_pos_cap = 0;
+    int graph_grid = 0;
+
+    std::mutex mu;
+
+    size_t device_bytes() const {
+        return ws.mem.bytes + outmem.bytes + in_cap * sizeof(tpc_hit) +
+               (sbuf[0] ? 2 * (carry_cap + chunk_cap) * (sizeof(tpc_hit) + sizeof(uint64_t)) : 0);
+    }
+};
+
+namespace {
+
+int grid_of(const tpc_ctx *c) {
+    int k = c->ctas_per_sm > 0 ? c->ctas_per_sm : 4;
+    return c->sms * k;
+}
+
+cudaError_t ensure_out(tpc_ctx *c, size_t n) {
+    if (n <= c->out_cap && c->d_labels) return cudaSuccess;
+    cudaStreamSynchronize(c->stream);
+    c->outmem.release();
+    cudaError_t e = cudaSuccess;
+    size_t cap = std::max<size_t>(n, 1024);
+    c->d_labels = c->outmem.alloc<uint64_t>(cap, e);
+    c->d_index = c->outmem.alloc<uint64_t>(cap, e);
+    c->d_rec = c->outmem.alloc<tpc_cluster>(cap, e);
+    if (e != cudaSuccess) {
+        c->outmem.release();
+        c->d_labels = c->d_index = nullptr;
+        c->d_rec = nullptr;
+        c->out_cap = 0;
+        return e;
+    }
+    c->out_cap = cap;
+    return cudaSuccess;
+}
+
+// Upload the host copy of the segment table through a pinned ring slot.
+cudaError_t upload_segs(tpc_ctx *c, const Work &w, const Seg *segs, int nsegs, cudaStream_t st) {
+    const int slot = c->seg_slot;
+    c->seg_slot = (c->seg_slot + 1) % SEG_RING;
+    cudaError_t e = cudaEventSynchronize(c->seg_ev[slot]);
+    if (e != cudaSuccess) return e;
+    Seg *h = c->h_seg + (size_t)slot * MAX_SEGS;
+    std::memcpy(h, segs, nsegs * sizeof(Seg));
+    e = cudaMemcpyAsync(w.seg, h, nsegs * sizeof(Seg), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecord(c->seg_ev[slot], st);
+}
+
+void enqueue_kernels(const Work &w, int nsegs, const Launch &L) {
+    launch_setup(w, nsegs, L.stream);
+    launch_prepare(w, L);
+    launch_seg_finalize(w, L.stream);
+    launch_make_keys(w, L);
+    for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
+    launch_gather(w, L);
+    launch_link(w, L);
+    launch_features(w, L);
+    launch_outputs(w, L);
+}
+
+// Run the fixed kernel sequence, from a CUDA graph captured on first use
+// (and re-captured when the workspace or the segment count changes).
+cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st) {
+    const Launch L{grid_of(owner), st};
+    if (!owner->graph || owner->graph_nsegs != nsegs || owner->graph_pos_cap != ws.pos_cap ||
+        owner->graph_grid != L.grid) {
+        if (owner->graph) {
+            cudaGraphExecDestroy(owner->graph);
+            owner->graph = nullptr;
+        }
+        cudaStream_t cap_st;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue_kernels(ws.w, nsegs, Launch{L.grid, cap_st});
+            e = cudaStreamEndCapture(cap_st, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&owner->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap_st);
+        if (e != cudaSuccess) {
+            owner->graph = nullptr;
+            return e;
+        }
+        owner->graph_nsegs = nsegs;
+        owner->graph_pos_cap = ws.pos_cap;
+        owner->graph_grid = L.grid;
+    }
+    return cudaGraphLaunch(owner->graph, st);
+}
+
+Seg base_seg(const tpc_ctx *c) {
+    Seg s{};
+    s.width = c->width;
+    s.height = c->height;
+    s.dt = c->dt32;
+    s.variant = (uint32_t)c->variant;
+    s.max_disorder = ~0ull;
+    return s;
+}
+
+cudaError_t stage_host(tpc_ctx *c, tpc_hit *dst, const tpc_hit *src, size_t n) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, src) == cudaSuccess && a.type == cudaMemoryTypeHost)
+        return cudaMemcpyAsync(dst, src, n * sizeof(tpc_hit), cudaMemcpyHostToDevice, c->stream);
+    cudaGetLastError();   // clear a possible "not a device pointer" error
+    const size_t chunk = size_t(1) << 20;
+    if (!c->h_stage) {
+        cudaError_t e = cudaMallocHost(&c->h_stage, chunk * sizeof(tpc_hit));
+        if (e != cudaSuccess) return e;
+        c->stage_cap = chunk;
+    }
+    for (size_t done = 0; done < n; done += chunk) {
+        const size_t m = std::min(chunk, n - done);
+        cudaError_t e = cudaEventSynchronize(c->stage_ev);
+        if (e != cudaSuccess) return e;
+        std::memcpy(c->h_stage, src + done, m * sizeof(tpc_hit));
+        e = cudaMemcpyAsync(dst + done, c->h_stage, m * sizeof(tpc_hit), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecord(c->stage_ev, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+bool over_budget(const tpc_ctx *c, size_t extra) {
+    return c->budget && c->device_bytes() + extra > c->budget;
+}
+
+// Make the pending hits of a non-streaming context live in c->in with room
+// for `more` additional hits.
+int materialise(tpc_ctx *c, size_t more) {
+    const size_t need = c->pending + more;
+    if (need > c->in_cap || (c->zc && !c->in)) {
+        size_t cap = std::max(need, c->in_cap * 2);
+        if (over_budget(c, (cap - c->in_cap) * sizeof(tpc_hit))) return TPC_ERR_BUSY;
+        tpc_hit *nb = nullptr;
+        if (cudaMalloc(&nb, cap * sizeof(tpc_hit)) != cudaSuccess) return TPC_ERR_NOMEM;
+        const tpc_hit *src = c->zc ? c->zc : c->in;
+        if (c->pending &&
+            cudaMemcpyAsync(nb, src, c->pending * sizeof(tpc_hit), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+            cudaFree(nb);
+            return TPC_ERR_CUDA;
+        }
+        if (c->in) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->in);
+        }
+        c->in = nb;
+        c->in_cap = cap;
+    } else if (c->zc) {
+        if (c->pending &&
+            cudaMemcpyAsync(c->in, c->zc, c->pending * sizeof(tpc_hit), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            return TPC_ERR_CUDA;
+    }
+    c->zc = nullptr;
+    return TPC_OK;
+}
+
+int ensure_stream_buffers(tpc_ctx *c, size_t chunk) {
+    if (chunk > c->chunk_cap || c->carry_ub + chunk > c->carry_cap) {
+        // learn the true carry size before growing anything
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+        uint32_t nc = 0;
+        if (c->ss && cudaMemcpy(&nc, &c->ss->n_carry, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return TPC_ERR_CUDA;
+        c->carry_ub = nc;
+    }
+    if (chunk <= c->chunk_cap && c->carry_ub + chunk <= c->carry_cap && c->sbuf[0]) return TPC_OK;
+    size_t ncarry = std::max<size_t>({c->carry_cap, 2 * (c->carry_ub + chunk), 1 << 16});
+    size_t nchunk = std::max<size_t>({c->chunk_cap, chunk, 1 << 16});
+    size_t extra = 2 * ((ncarry + nchunk) - (c->carry_cap + c->chunk_cap)) * (sizeof(tpc_hit) + sizeof(uint64_t));
+    if (over_budget(c, extra)) return TPC_ERR_BUSY;
+    tpc_hit *nb[2] = {nullptr, nullptr};
+    uint64_t *ng[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMalloc(&nb[i], (ncarry + nchunk) * sizeof(tpc_hit)) != cudaSuccess ||
+            cudaMalloc(&ng[i], (ncarry + nchunk) * sizeof(uint64_t)) != cudaSuccess) {
+            for (int j = 0; j < 2; ++j) { cudaFree(nb[j]); cudaFree(ng[j]); }
+            return TPC_ERR_NOMEM;
+        }
+    }
+    // move the current carry (right aligned in the buffer the next step reads)
+    const int next = 1 - c->scur;
+    if (c->sbuf[next] && c->carry_ub) {
+        const size_t nc = c->carry_ub;   // exact after the synchronisation above
+        cudaMemcpyAsync(nb[next] + (ncarry - nc), c->sbuf[next] + (c->carry_cap - nc), nc * sizeof(tpc_hit),
+                        cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(ng[next] + (ncarry - nc), c->sgidx[next] + (c->carry_cap - nc), nc * sizeof(uint64_t),
+                        cudaMemcpyDeviceToDevice, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(c->sbuf[i]);
+        cudaFree(c->sgidx[i]);
+        c->sbuf[i] = nb[i];
+        c->sgidx[i] = ng[i];
+    }
+    c->carry_cap = ncarry;
+    c->chunk_cap = nchunk;
+    return TPC_OK;
+}
+
+// One streaming step over the carry plus `n` new hits already copied into
+// the chunk region of the next input buffer.  close_all: end of stream.
+int stream_step(tpc_ctx *c, size_t n, bool close_all) {
+    const int in = 1 - c->scur;
+    const size_t positions = c->carry_ub + n;
+    if (c->ws.ensure(positions) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (ensure_out(c, c->carry_cap + c->chunk_cap) != cudaSuccess) return TPC_ERR_NOMEM;
+    Seg s = base_seg(c);
+    s.carry_in = c->sbuf[in];
+    s.carry_gidx_in = c->sgidx[in];
+    s.carry_out = c->sbuf[c->scur];
+    s.carry_gidx_out = c->sgidx[c->scur];
+    s.ss = c->ss;
+    s.out_labels = c->d_labels;
+    s.out_index = c->d_index;
+    s.out_rec = c->d_rec;
+    s.out_cap = (uint32_t)c->out_cap;
+    s.gidx_base = c->pushed;
+    s.max_disorder = close_all ? ~0ull : c->max_disorder;
+    s.carry_cap = (uint32_t)c->carry_cap;
+    s.n_new = (uint32_t)n;
+    if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (run_step(c, c->ws, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    c->scur = in;
+    c->pushed += n;
+    c->carry_ub = close_all ? 0 : positions;
+    c->res_seg = c->ws.w.seg;
+    c->res_prob = c->ws.w.prob;
+    c->has_result = true;
+    c->res_streaming = true;
+    return TPC_OK;
+}
+
+struct ResultInfo {
+    Seg seg;
+    Prob prob;
+};
+
+int read_result(tpc_ctx *c, ResultInfo &r) {
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (!c->has_result) {
+        std::memset(&r, 0, sizeof(r));
+        return TPC_OK;
+    }
+    if (cudaMemcpy(&r.seg, c->res_seg, sizeof(Seg), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&r.prob, c->res_prob, sizeof(Prob), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TPC_ERR_CUDA;
+    return map_err(r.prob.err);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tpc_create(uint32_t width, uint32_t height, uint64_t dt, int variant, tpc_ctx **out) {
+    if (!out) return TPC_ERR_ARG;
+    *out = nullptr;
+    if (width == 0 || height == 0 || width > 65536 || height > 65536 ||
+        (uint64_t)width * height > MAX_PIXELS)
+        return TPC_ERR_ARG;
+    if (variant != TPC_LOCAL && variant != TPC_GLOBAL && variant != TPC_STATIC) return TPC_ERR_ARG;
+    tpc_ctx *c = new (std::nothrow) tpc_ctx();
+    if (!c) return TPC_ERR_NOMEM;
+    c->width = width;
+    c->height = height;
+    c->dt = dt;
+    c->dt32 = dt > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)dt;
+    c->variant = variant;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return TPC_ERR_CUDA; }
+    c->sms = num_sms(c->device);
+    if (init_kernel_attributes() != cudaSuccess) { delete c; return TPC_ERR_CUDA; }
+    bool ok = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess;
+    c->own_stream = ok;
+    ok = ok && cudaMallocHost(&c->h_seg, sizeof(Seg) * MAX_SEGS * SEG_RING) == cudaSuccess;
+    for (int i = 0; ok && i < SEG_RING; ++i)
+        ok = cudaEventCreateWithFlags(&c->seg_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { tpc_destroy(c); return TPC_ERR_CUDA; }
+    *out = c;
+    return TPC_OK;
+}
+
+int tpc_set_option(tpc_ctx *c, int key, uint64_t value) {
+    if (!c) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const bool busy = c->pending || c->zc || (c->ss && c->carry_ub);
+    switch (key) {
+    case TPC_OPT_MAX_DISORDER:
+        if (busy) return TPC_ERR_STATE;
+        if (value == 0) return TPC_ERR_ARG;
+        c->max_disorder = value;
+        if (value != ~0ull && !c->ss) {
+            if (cudaMalloc(&c->ss, sizeof(StreamState)) != cudaSuccess) return TPC_ERR_NOMEM;
+            if (cudaMemsetAsync(c->ss, 0, sizeof(StreamState), c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+            c->scur = 1;
+            c->carry_ub = 0;
+        }
+        return TPC_OK;
+    case TPC_OPT_MEM_BUDGET:
+        c->budget = value;
+        return TPC_OK;
+    case TPC_OPT_STREAM: {
+        if (busy) return TPC_ERR_STATE;
+        cudaStreamSynchronize(c->stream);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        c->own_stream = false;
+        c->stream = reinterpret_cast<cudaStream_t>(value);
+        if (!value) {
+            if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return TPC_ERR_CUDA;
+            c->own_stream = true;
+        }
+        return TPC_OK;
+    }
+    case TPC_OPT_CTAS_PER_SM:
+        if (value > 64) return TPC_ERR_ARG;
+        c->ctas_per_sm = (int)value;
+        return TPC_OK;
+    default:
+        return TPC_ERR_ARG;
+    }
+}
+
+int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
+    if (!c || (n && !hits) || (where != TPC_HOST && where != TPC_DEVICE)) return TPC_ERR_ARG;
+    if (n > 0x7FFFFFFFull) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->max_disorder != ~0ull) {
+        // streaming: copy the chunk behind the carry and cluster it now
+        if (c->variant != TPC_LOCAL) return TPC_ERR_ARG;
+        if (c->budget && over_budget(c, Workspace::bytes_for(c->carry_ub + n) > c->ws.mem.bytes
+                                            ? Workspace::bytes_for(c->carry_ub + n) - c->ws.mem.bytes : 0))
+            return TPC_ERR_BUSY;
+        int rc = ensure_stream_buffers(c, n);
+        if (rc) return rc;
+        tpc_hit *dst = c->sbuf[1 - c->scur] + c->carry_cap;
+        cudaError_t e = where == TPC_HOST
+            ? stage_host(c, dst, hits, n)
+            : cudaMemcpyAsync(dst, hits, n * sizeof(tpc_hit), cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return TPC_ERR_CUDA;
+        return stream_step(c, n, false);
+    }
+    if (n == 0) return TPC_OK;
+    if (where == TPC_DEVICE && c->pending == 0 && !c->zc) {
+        c->zc = hits;   // zero copy: read in place by the next flush
+        c->pending = n;
+        return TPC_OK;
+    }
+    int rc = materialise(c, n);
+    if (rc) return rc;
+    cudaError_t e = where == TPC_HOST
+        ? stage_host(c, c->in + c->pending, hits, n)
+        : cudaMemcpyAsync(c->in + c->pending, hits, n * sizeof(tpc_hit), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return TPC_ERR_CUDA;
+    c->pending += n;
+    return TPC_OK;
+}
+
+int tpc_flush(tpc_ctx *c) {
+    if (!c) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->max_disorder != ~0ull) {
+        int rc = ensure_stream_buffers(c, 0);
+        if (rc) return rc;
+        return stream_step(c, 0, true);
+    }
+    if (c->variant != TPC_LOCAL) return TPC_ERR_ARG;
+    const size_t n = c->pending;
+    if (over_budget(c, Workspace::bytes_for(n) > c->ws.mem.bytes ? Workspace::bytes_for(n) - c->ws.mem.bytes : 0))
+        return TPC_ERR_BUSY;
+    if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
+    Seg s = base_seg(c);
+    s.hits = c->zc ? c->zc : c->in;
+    s.out_labels = c->d_labels;
+    s.out_rec = c->d_rec;
+    s.out_cap = (uint32_t)c->out_cap;
+    s.gidx_base = c->pushed;
+    s.n_new = (uint32_t)n;
+    if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (run_step(c, c->ws, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    c->res_base = c->pushed;
+    c->pushed += n;
+    c->pending = 0;
+    c->zc = nullptr;
+    c->res_seg = c->ws.w.seg;
+    c->res_prob = c->ws.w.prob;
+    c->has_result = true;
+    c->res_streaming = false;
+    return TPC_OK;
+}
+
+int tpc_sync(tpc_ctx *c) {
+    if (!c) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    ResultInfo r;
+    return read_result(c, r);
+}
+
+int tpc_counts(tpc_ctx *c, size_t *n_hits, size_t *n_clusters, size_t *n_open) {
+    if (!c) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    ResultInfo r;
+    int rc = read_result(c, r);
+    if (n_hits) *n_hits = r.seg.n_final;
+    if (n_clusters) *n_clusters = r.seg.n_clusters;
+    if (n_open) *n_open = r.seg.n_open;
+    return rc;
+}
+
+int tpc_labels(tpc_ctx *c, uint64_t *labels, uint64_t *indices, size_t cap, size_t *n_out, int where) {
+    if (!c || !n_out || (where != TPC_HOST && where != TPC_DEVICE)) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    ResultInfo r;
+    int rc = read_result(c, r);
+    if (rc) return rc;
+    const size_t n = r.seg.n_final;
+    *n_out = n;
+    if (n > cap) return TPC_ERR_CAP;
+    if (n && !labels) return TPC_ERR_ARG;
+    if (!n) return TPC_OK;
+    const cudaMemcpyKind kind = where == TPC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(labels, c->d_labels, n * sizeof(uint64_t), kind, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (indices) {
+        if (c->res_streaming) {
+            if (cudaMemcpyAsync(indices, c->d_index, n * sizeof(uint64_t), kind, c->stream) != cudaSuccess)
+                return TPC_ERR_CUDA;
+        } else if (where == TPC_DEVICE) {
+            k_iota_u64<<<c->sms * 4, 256, 0, c->stream>>>(indices, c->res_base, n);
+        } else {
+            for (size_t i = 0; i < n; ++i) indices[i] = c->res_base + i;
+        }
+    }
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
+}
+
+int tpc_cluster_features(tpc_ctx *c, tpc_cluster *out, size_t cap, size_t *n_out, int where) {
+    if (!c || !n_out || (where != TPC_HOST && where != TPC_DEVICE)) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    ResultInfo r;
+    int rc = read_result(c, r);
+    if (rc) return rc;
+    const size_t n = r.seg.n_clusters;
+    *n_out = n;
+    if (n > cap) return TPC_ERR_CAP;
+    if (n && !out) return TPC_ERR_ARG;
+    if (!n) return TPC_OK;
+    const cudaMemcpyKind kind = where == TPC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(out, c->d_rec, n * sizeof(tpc_cluster), kind, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
+}
+
+int tpc_batch_flush(tpc_ctx **ctxs, int n) {
+    if (!ctxs || n <= 0 || n > MAX_SEGS) return TPC_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || ctxs[i]->max_disorder != ~0ull || ctxs[i]->variant != TPC_LOCAL) return TPC_ERR_ARG;
+        for (int j = 0; j < i; ++j) if (ctxs[j] == ctxs[i]) return TPC_ERR_ARG;
+        if (ctxs[i]->device != ctxs[0]->device) return TPC_ERR_ARG;
+    }
+    tpc_ctx *lead = ctxs[0];
+    std::vector<std::unique_lock<std::mutex>> locks;
+    for (int i = 0; i < n; ++i) locks.emplace_back(ctxs[i]->mu);
+    size_t positions = 0;
+    for (int i = 0; i < n; ++i) positions += ((ctxs[i]->pending + TILE - 1) / TILE) * TILE;
+    // every context's pending copies must land before the lead stream reads them
+    for (int i = 1; i < n; ++i) {
+        if (cudaEventRecord(ctxs[i]->done_ev, ctxs[i]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(lead->stream, ctxs[i]->done_ev, 0) != cudaSuccess)
+            return TPC_ERR_CUDA;
+    }
+    if (lead->ws.ensure(positions) != cudaSuccess) return TPC_ERR_NOMEM;
+    std::vector<Seg> segs(n);
+    for (int i = 0; i < n; ++i) {
+        tpc_ctx *c = ctxs[i];
+        if (ensure_out(c, c->pending) != cudaSuccess) return TPC_ERR_NOMEM;
+        Seg s = base_seg(c);
+        s.hits = c->zc ? c->zc : c->in;
+        s.out_labels = c->d_labels;
+        s.out_rec = c->d_rec;
+        s.out_cap = (uint32_t)c->out_cap;
+        s.gidx_base = c->pushed;
+        s.n_new = (uint32_t)c->pending;
+        segs[i] = s;
+    }
+    if (upload_segs(lead, lead->ws.w, segs.data(), n, lead->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (run_step(lead, lead->ws, n, lead->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (cudaEventRecord(lead->done_ev, lead->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+        tpc_ctx *c = ctxs[i];
+        if (i && cudaStreamWaitEvent(c->stream, lead->done_ev, 0) != cudaSuccess) return TPC_ERR_CUDA;
+        c->res_base = c->pushed;
+        c->pushed += c->pending;
+        c->pending = 0;
+        c->zc = nullptr;
+        c->res_seg = lead->ws.w.seg + i;
+        c->res_prob = lead->ws.w.prob;
+        c->has_result = true;
+        c->res_streaming = false;
+    }
+    return TPC_OK;
+}
+
+int tpc_device_bytes(tpc_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    *bytes = c->device_bytes();
+    return TPC_OK;
+}
+
+const char *tpc_strerror(int status) {
+    switch (status) {
+    case TPC_OK: return "ok";
+    case TPC_ERR_ARG: return "invalid argument";
+    case TPC_ERR_RANGE: return "hit outside the sensor";
+    case TPC_ERR_NOMEM: return "out of device or pinned memory";
+    case TPC_ERR_BUSY: return "memory budget exceeded";
+    case TPC_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TPC_ERR_CUDA: return "CUDA runtime error";
+    case TPC_ERR_CAP: return "output buffer too small";
+    case TPC_ERR_SPAN: return "ToA span of one step is 2^32 ticks or more";
+    case TPC_ERR_LATE: return "hit later than max_disorder allows";
+    case TPC_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown status";
+    }
+}
+
+void tpc_destroy(tpc_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->ws.mem.release();
+    c->outmem.release();
+    cudaFree(c->in);
+    for (int i = 0; i < 2; ++i) { cudaFree(c->sbuf[i]); cudaFree(c->sgidx[i]); }
+    cudaFree(c->ss);
+    if (c->h_seg) cudaFreeHost(c->h_seg);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (int i = 0; i < SEG_RING; ++i) if (c->seg_ev[i]) cudaEventDestroy(c->seg_ev[i]);
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    if (c->done_ev) cudaEventDestroy(c->done_ev);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// Internal layout shared by the kernels and the host orchestration of libtpc.
+//
+// Positions.  A processing step clusters one or more independent segments
+// (one per sensor / context).  Their hits live in separate input buffers but
+// every work array is indexed by a single "position" space in which segment
+// s occupies [off, off + n) and off is a multiple of TILE, so that tiles,
+// 32-position flag words and warps never straddle two segments.
+//
+// Within a segment, position p stands for input hit (p - off).  After the
+// ToA sort, sorted position s holds the hit whose position is sidx[s]; the
+// union-find forest lives on sorted positions and a root is the earliest hit
+// of its cluster in (ToA, index) order, the paper's "time invariant"
+// toa(h) >= toa(parent(h)) (Section 4.1).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tpc.h"
+
+namespace tpc {
+
+constexpr int TILE = 4096;          // positions per tile (sort, link, flags)
+constexpr int TILE_WORDS = TILE / 32;
+constexpr int MAX_SEGS = 256;
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr uint32_t MAX_PIXELS = 1u << 20;   // width*height bound (packed smem keys)
+
+enum ErrBits : uint32_t {
+    E_RANGE = 1u,     // hit outside the sensor
+    E_SPAN = 2u,      // ToA span of a segment >= 2^32
+    E_LATE = 4u,      // streaming: chunk ToA below the last watermark
+    E_TIMEOUT = 8u,   // a bounded wait gave up
+    E_CAP = 16u,      // internal capacity exceeded
+};
+
+// Carried state of a streaming context (device resident across steps).
+struct StreamState {
+    uint32_t n_carry;         // open hits carried into the next step
+    uint32_t has_seen;        // seen_max is valid
+    uint64_t seen_max;        // max ToA over all pushed hits
+    uint64_t watermark;       // clusters with last ToA <= watermark are final
+};
+
+enum CloseMode : uint32_t { CLOSE_NONE = 0, CLOSE_ALL = 1, CLOSE_WM = 2 };
+
+struct Seg {
+    // ---- set by the host ----------------------------------------------
+    const tpc_hit *hits;       // input hits [0, n); for streaming: set on device
+    const tpc_hit *carry_in;   // streaming: buffer whose [cap - n_carry, cap) holds the carry
+    const uint64_t *carry_gidx_in;
+    tpc_hit *carry_out;        // streaming: next step's buffer (carry written right aligned)
+    uint64_t *carry_gidx_out;
+    StreamState *ss;           // streaming state, null when not streaming
+    uint64_t *out_labels;      // finalised labels (u64), ordered by global index
+    uint64_t *out_index;       // their global indices (streaming only; may be null)
+    tpc_cluster *out_rec;      // finalised cluster records ordered by label
+    uint64_t gidx_base;        // global index of the first new hit
+    uint64_t max_disorder;     // UINT64_MAX: not streaming (everything closes)
+    uint32_t carry_cap;        // streaming: capacity of the carry region
+    uint32_t n_new;            // hits pushed in this step
+    uint32_t width, height;
+    uint32_t dt;               // time window, clamped to 32 bits
+    uint32_t variant;
+    uint32_t out_cap;          // capacity of out_labels/out_index and out_rec
+    uint32_t close_mode;       // CloseMode, derived on the device
+    // ---- derived on the device ------------------------------------------
+    const uint64_t *carry_gidx;  // global indices of hits [0, n_carry)
+    uint32_t n_carry;
+    uint32_t n;                // n_carry + n_new
+    uint32_t off;              // first position
+    uint32_t tile0, ntiles;
+    uint32_t npasses;          // radix passes this segment needs
+    uint64_t toa_min, toa_max;
+    uint64_t chunk_min;        // min ToA of the new hits
+    uint64_t watermark;        // CLOSE_WM: close clusters whose last ToA <= watermark
+    uint64_t seen_after;       // streaming: max ToA seen after this step
+    // ---- outputs -------------------------------------------------------
+    uint32_t n_final;          // hits finalised
+    uint32_t n_clusters;       // clusters finalised
+    uint32_t n_open;           // hits carried forward
+    uint32_t pad1;
+};
+
+struct Prob {
+    uint32_t nsegs;
+    uint32_t ntiles;
+    uint32_t npasses;      // max over segments; sorted data in buffer npasses % 2
+    uint32_t err;          // ErrBits
+    uint32_t tile_cap;
+    uint32_t pos_cap;
+};
+
+// Work arrays (device), sized for pos_cap positions and tile_cap tiles.
+struct Work {
+    Seg *seg;
+    Prob *prob;
+    uint32_t *tile_seg;        // [tile_cap]
+    uint32_t *keys[2];         // radix ping-pong: ToA - toa_min
+    uint32_t *vals[2];         // radix ping-pong: position
+    uint32_t *spix;            // sorted positions: x | y << 16
+    uint32_t *parent;          // union-find over sorted positions
+    uint32_t *root_of;         // per position: root (a sorted position)
+    uint32_t *slot_size;       // per root
+    uint32_t *slot_min;        // per root: smallest position
+    uint32_t *slot_maxkey;     // per root: largest key (last ToA - toa_min)
+    unsigned long long *slot_tot, *slot_wx, *slot_wy;
+    uint64_t *lab_tmp;         // streaming: label per position
+    uint32_t *flag_label;      // bit per position: label hit of a finalised cluster
+    uint32_t *flag_closed;     // bit per position: hit of a finalised cluster
+    uint32_t *tile_cnt;        // [2][tile_cap] counts of the two flag kinds
+    uint32_t *tile_base;       // [2][tile_cap] exclusive per-segment prefix
+    uint32_t *hist;            // [RADIX][tile_cap]
+    uint32_t *segtot;          // [MAX_SEGS][RADIX]
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+
+__device__ __forceinline__ uint32_t seg_of_tile(const Work &w, uint32_t t) { return w.tile_seg[t]; }
+
+__device__ __forceinline__ void tile_range(const Seg &s, uint32_t t, uint32_t &begin, uint32_t &end) {
+    begin = s.off + (t - s.tile0) * (uint32_t)TILE;
+    uint32_t e = begin + (uint32_t)TILE, last = s.off + s.n;
+    end = e < last ? e : last;
+}
+
+__device__ __forceinline__ uint64_t gidx_of(const Seg &s, uint32_t local) {
+    return local < s.n_carry ? s.carry_gidx[local] : s.gidx_base + (local - s.n_carry);
+}
+
+__device__ __forceinline__ uint32_t sorted_sel(const Prob &p) { return p.npasses & 1u; }
+
+// Union-find on global memory over sorted positions.  Roots are the smaller
+// position (hook the larger root under the smaller, Jaiganesh & Burtscher,
+// "A high-performance connected components implementation for GPUs", 2018);
+// path halving on every find.
+__device__ __forceinline__ uint32_t gfind(uint32_t *parent, uint32_t x) {
+    volatile uint32_t *par = parent;
+    while (true) {
+        uint32_t p = par[x];
+        if (p == x) return x;
+        uint32_t gp = par[p];
+        if (gp == p) return p;
+        par[x] = gp;
+        x = gp;
+    }
+}
+
+__device__ __forceinline__ void gunion(uint32_t *parent, uint32_t a, uint32_t b) {
+    while (true) {
+        a = gfind(parent, a);
+        b = gfind(parent, b);
+        if (a == b) return;
+        if (a > b) { uint32_t t = a; a = b; b = t; }
+        uint32_t old = atomicCAS(parent + b, b, a);
+        if (old == b) return;
+    }
+}
+
+__device__ __forceinline__ uint32_t sfind(uint32_t *parent, uint32_t x) {
+    volatile uint32_t *par = parent;
+    while (true) {
+        uint32_t p = par[x];
+        if (p == x) return x;
+        uint32_t gp = par[p];
+        if (gp == p) return p;
+        par[x] = gp;
+        x = gp;
+    }
+}
+
+__device__ __forceinline__ void sunion(uint32_t *parent, uint32_t a, uint32_t b) {
+    while (true) {
+        a = sfind(parent, a);
+        b = sfind(parent, b);
+        if (a == b) return;
+        if (a > b) { uint32_t t = a; a = b; b = t; }
+        uint32_t old = atomicCAS(parent + b, b, a);
+        if (old == b) return;
+    }
+}
+
+__device__ __forceinline__ uint4 ld_hit(const tpc_hit *h) {
+    return __ldg(reinterpret_cast<const uint4 *>(h));
+}
+__device__ __forceinline__ uint32_t hit_x(uint4 v) { return v.x & 0xFFFFu; }
+__device__ __forceinline__ uint32_t hit_y(uint4 v) { return v.x >> 16; }
+__device__ __forceinline__ uint32_t hit_tot(uint4 v) { return v.y & 0xFFFFu; }
+__device__ __forceinline__ uint64_t hit_toa(uint4 v) { return ((uint64_t)v.w << 32) | v.z; }
+
+// ---------------------------------------------------------------------------
+// host-side launchers (one translation unit each)
+
+struct Launch {
+    int grid;          // persistent CTAs
+    cudaStream_t stream;
+};
+
+cudaError_t init_kernel_attributes();   // once per process and device, before capture
+void launch_setup(const Work &w, int nsegs, cudaStream_t st);
+void launch_prepare(const Work &w, const Launch &L);
+void launch_seg_finalize(const Work &w, cudaStream_t st);
+void launch_make_keys(const Work &w, const Launch &L);
+void launch_radix_pass(const Work &w, int pass, const Launch &L);
+void launch_gather(const Work &w, const Launch &L);
+void launch_link(const Work &w, const Launch &L);
+void launch_features(const Work &w, const Launch &L);
+void launch_outputs(const Work &w, const Launch &L);
+
+}  // namespace tpc

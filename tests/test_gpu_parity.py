@@ -1,0 +1,184 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Labels must match bit-exactly; size, sum ToT and first ToA exactly; the fp32
+centroids within 1e-5 relative of the fp64 oracle.  Sizes span several tiles
+(4096 hits) with ragged tails; edge cases cover empty and single inputs,
+degenerate piles on one pixel or one ToA, sensor borders, ToA near 2^64 and
+the error paths.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from bruteforce import random_hits
+from gpu_helpers import (assert_features_equal, check_against_oracle, run_gpu,
+                         sampled_cluster_check)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2412_11809_gb300 import Clusterer, TpcError  # noqa: E402
+
+
+def test_cfg0_full_size():
+    hits, _ = synth.cfg0()
+    check_against_oracle(hits, 256, 256, synth.DT_200NS)
+
+
+def test_cfg1_scaled():
+    hits, _ = synth.cfg1(scale=1 / 16)
+    check_against_oracle(hits, 256, 256, synth.DT_200NS)
+
+
+def test_cfg4_timepix4_scaled_both_windows():
+    hits, _ = synth.cfg4(scale=1 / 256)
+    check_against_oracle(hits, 448, 512, synth.DT_200NS)
+    check_against_oracle(hits, 448, 512, synth.DT_600NS)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 4095, 4096, 4097, 8191, 12289, 40000])
+def test_ragged_sizes(n):
+    rng = np.random.default_rng(n)
+    hits = random_hits(rng, n, 40, 30, max(1, n * 3))
+    check_against_oracle(hits, 40, 30, 7)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_dense_small_sensor(seed):
+    """Tiny sensors and dense time: long same-pixel chains, halos spanning tiles."""
+    rng = np.random.default_rng(100 + seed)
+    w, h = int(rng.integers(1, 9)), int(rng.integers(1, 9))
+    n = int(rng.integers(5000, 30000))
+    hits = random_hits(rng, n, w, h, int(rng.integers(0, 4 * n)))
+    check_against_oracle(hits, w, h, int(rng.integers(0, 50)))
+
+
+def test_pile_on_one_pixel():
+    n = 20000
+    hits = oracle.make_hits(np.zeros(n, int), np.zeros(n, int), np.arange(n)[::-1] * 3)
+    lab, _ = check_against_oracle(hits, 1, 1, 3)
+    assert len(np.unique(lab)) == 1
+    lab, _ = check_against_oracle(hits, 1, 1, 2)
+    assert len(np.unique(lab)) == n
+
+
+def test_all_same_toa_is_pixel_ccl():
+    rng = np.random.default_rng(7)
+    hits = random_hits(rng, 30000, 200, 150, 0)
+    hits["toa"] = 123456789
+    check_against_oracle(hits, 200, 150, 0)
+
+
+def test_borders_and_corners():
+    rng = np.random.default_rng(8)
+    W, H = 64, 48
+    xs = rng.choice([0, 1, W - 2, W - 1], 20000)
+    ys = rng.choice([0, 1, H - 2, H - 1], 20000)
+    hits = oracle.make_hits(xs, ys, rng.integers(0, 200000, 20000), rng.integers(1, 100, 20000))
+    check_against_oracle(hits, W, H, 10)
+
+
+def test_toa_near_top_of_range():
+    rng = np.random.default_rng(9)
+    hits = random_hits(rng, 10000, 32, 32, 50000)
+    hits["toa"] += np.uint64(2**64 - 60000)
+    check_against_oracle(hits, 32, 32, 20)
+
+
+def test_dt_zero_and_huge():
+    hits, _ = synth.cfg0(scale=0.02, seed=3)
+    check_against_oracle(hits, 256, 256, 0)
+    check_against_oracle(hits, 256, 256, 2**40)
+
+
+def test_host_push_and_multiple_pushes():
+    hits, _ = synth.cfg0(scale=0.05, seed=4)
+    want = oracle.labels(hits, 256, 256, 128)
+    for device, pushes in ((False, 1), (False, 3), (True, 5)):
+        lab, feats = run_gpu(hits, 256, 256, 128, device=device, pushes=pushes)
+        np.testing.assert_array_equal(lab, want)
+
+
+def test_input_permutation():
+    hits, _ = synth.cfg1(scale=1 / 256, seed=5)
+    perm = np.random.default_rng(0).permutation(len(hits))
+    check_against_oracle(hits[perm], 256, 256, 128)
+
+
+def test_empty_flush():
+    with Clusterer(256, 256, 128) as c:
+        c.flush()
+        assert c.counts() == (0, 0, 0)
+        assert len(c.labels()) == 0 and len(c.features()) == 0
+
+
+def test_out_of_range_reported():
+    hits = oracle.make_hits([1, 300], [1, 1], [5, 6])
+    with Clusterer(256, 256, 128) as c:
+        c.push(hits)
+        c.flush()
+        with pytest.raises(TpcError) as e:
+            c.sync()
+        assert e.value.name == "TPC_ERR_RANGE"
+
+
+def test_span_too_large_reported():
+    hits = oracle.make_hits([1, 2], [1, 1], [0, 2**33])
+    with Clusterer(256, 256, 128) as c:
+        c.push(hits)
+        c.flush()
+        with pytest.raises(TpcError) as e:
+            c.sync()
+        assert e.value.name == "TPC_ERR_SPAN"
+
+
+def test_bad_arguments():
+    with pytest.raises(TpcError):
+        Clusterer(0, 256, 128)
+    with pytest.raises(TpcError):
+        Clusterer(4096, 4096, 128)   # more than 2^20 pixels
+    with pytest.raises(KeyError):
+        Clusterer(256, 256, 128, "nonsense")
+
+
+def test_repeat_flushes_continue_global_indices():
+    a, _ = synth.cfg0(scale=0.01, seed=11)
+    b, _ = synth.cfg0(scale=0.01, seed=12)
+    with Clusterer(256, 256, 128) as c:
+        c.push(a)
+        c.flush()
+        la = c.labels()
+        c.push(b)
+        c.flush()
+        lb, ib = c.labels(with_indices=True)
+    np.testing.assert_array_equal(la, oracle.labels(a, 256, 256, 128))
+    np.testing.assert_array_equal(ib, np.arange(len(a), len(a) + len(b)))
+    np.testing.assert_array_equal(lb, oracle.labels(b, 256, 256, 128) + len(a))
+
+
+@pytest.mark.slow
+def test_cfg1_full_size_sampled():
+    """The benchmark workload at full size (64M hits), in the launch
+    configuration the benchmark uses; exact checks of sampled clusters plus
+    properties that hold at any size."""
+    hits, _ = synth.cfg1()
+    dev = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).cuda()
+    with Clusterer(256, 256, synth.DT_200NS) as c:
+        c.push(dev)
+        c.flush()
+        lab = c.labels()
+        feats = c.features()
+    n = len(hits)
+    idx = np.arange(n, dtype=np.uint64)
+    assert np.all(lab <= idx)
+    assert np.all(lab[lab.astype(np.int64)] == lab)
+    assert feats["size"].sum() == n
+    assert feats["sum_tot"].sum() == hits["tot"].astype(np.int64).sum()
+    np.testing.assert_array_equal(feats["label"], np.unique(lab))
+    checked = sampled_cluster_check(hits, lab, 256, 256, synth.DT_200NS, 150,
+                                    np.random.default_rng(1))
+    assert checked > 50
