@@ -150,6 +150,15 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n);
    the last processing step.  Waits for the context's work. */
 int tpc_counts(tpc_ctx *ctx, size_t *n_hits, size_t *n_clusters, size_t *n_open);
 
+/* Diagnostics: tpc_flush() with the kernels launched one by one (no CUDA
+   graph) and an event after each; names[k] (static strings) and ms[k]
+   receive each kernel's device time in launch order, *n_out the number of
+   kernels in one processing step.  Waits for completion.  TPC_ERR_CAP if
+   cap < *n_out (the first cap entries are written); TPC_ERR_STATE for a
+   streaming context.  Not part of the paper: per-kernel timing in the
+   spirit of its wall-clock measurements (Section 4, benchmark set-up). */
+int tpc_profile_flush(tpc_ctx *ctx, const char **names, float *ms, int cap, int *n_out);
+
 /* Bytes of device memory the context currently holds. */
 int tpc_device_bytes(tpc_ctx *ctx, size_t *bytes);
 

@@ -41,6 +41,8 @@ SIGNATURES = {
     "tpc_batch_flush": ([ctypes.POINTER(_VP), _INT], _INT),
     "tpc_counts": ([_VP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)], _INT),
     "tpc_device_bytes": ([_VP, ctypes.POINTER(_SZ)], _INT),
+    "tpc_profile_flush": ([_VP, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
+                           _INT, ctypes.POINTER(_INT)], _INT),
     "tpc_strerror": ([_INT], ctypes.c_char_p),
     "tpc_destroy": ([_VP], None),
 }
@@ -137,8 +139,28 @@ class Clusterer:
             _check(self._lib.tpc_push(self._h, a.ctypes.data if len(a) else None, len(a), TPC_HOST),
                    "tpc_push")
 
+    def push_ptr(self, ptr: int, n: int, device: bool):
+        """Append n hits from a raw pointer (host or device memory)."""
+        _check(self._lib.tpc_push(self._h, ptr, n, TPC_DEVICE if device else TPC_HOST), "tpc_push")
+
     def flush(self):
         _check(self._lib.tpc_flush(self._h), "tpc_flush")
+
+    def labels_into(self, labels_ptr: int, cap: int, device: bool, indices_ptr: int | None = None) -> int:
+        """Write the last step's labels into caller memory; returns the count."""
+        n_out = ctypes.c_size_t()
+        rc = self._lib.tpc_labels(self._h, labels_ptr, indices_ptr, cap, ctypes.byref(n_out),
+                                  TPC_DEVICE if device else TPC_HOST)
+        self._keep.clear()
+        _check(rc, "tpc_labels")
+        return n_out.value
+
+    def features_into(self, rec_ptr: int, cap: int, device: bool) -> int:
+        """Write the last step's cluster records into caller memory; returns the count."""
+        n_out = ctypes.c_size_t()
+        _check(self._lib.tpc_cluster_features(self._h, rec_ptr, cap, ctypes.byref(n_out),
+                                              TPC_DEVICE if device else TPC_HOST), "features")
+        return n_out.value
 
     def sync(self):
         rc = self._lib.tpc_sync(self._h)
@@ -185,6 +207,16 @@ class Clusterer:
             _check(self._lib.tpc_cluster_features(self._h, rec.ctypes.data if m else None, m,
                                                   ctypes.byref(n_out), TPC_HOST), "features")
         return rec
+
+    def profile_flush(self) -> list[tuple[str, float]]:
+        """Like flush(), kernels launched one by one; returns (kernel, ms) in order."""
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_float * cap)()
+        n = ctypes.c_int()
+        _check(self._lib.tpc_profile_flush(self._h, names, ms, cap, ctypes.byref(n)),
+               "tpc_profile_flush")
+        return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
 
     def device_bytes(self) -> int:
         b = ctypes.c_size_t()

@@ -1,13 +1,12 @@
 // Per-cluster features, canonical labels and stream compaction.
 //
-// k_accumulate walks the hits in input order (16-byte coalesced loads) and
-// reduces size, sum ToT, sum ToT*x, sum ToT*y, smallest position and largest
-// key into the root's slot.  Hits of one cluster that share a warp are
-// combined first (match.any + redux.sync), so one lane per cluster and warp
-// issues the atomics.  Integer sums are exact; the centroid is one division
-// of exact sums (features are the purpose named in Section 1: on-the-fly
-// filtering and compression; Algorithm 3 step 6 orders clusters by time,
-// here records are ordered by label instead).
+// k_accumulate walks the hits in (ToA, position) order and reduces size,
+// sum ToT, sum ToT*x, sum ToT*y, smallest position and largest key into the
+// root's slot, privatised in shared memory per span of sorted positions.
+// Integer sums are exact; the centroid is one division of exact sums
+// (features are the purpose named in Section 1: on-the-fly filtering and
+// compression; Algorithm 3 step 6 orders clusters by time, here records are
+// ordered by label instead).
 //
 // k_labels writes label = global index of the smallest position of the
 // cluster and sets two bit flags per position (label hit of a finalised
@@ -19,50 +18,91 @@
 
 namespace tpc {
 
-__device__ __forceinline__ uint32_t lanemask_lt_f() {
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
+constexpr int ACC_THREADS = 256;
+constexpr int ACC_SPAN = 2048;                    // sorted positions per pass
+constexpr int ACC_ITEMS = ACC_SPAN / ACC_THREADS;
+constexpr int ACC_SMEM = 8 * ACC_SPAN * (int)sizeof(uint32_t);
 
-// Sum of a 32-bit value over `peers` without overflow (< 2^32 each, <= 32 lanes).
-__device__ __forceinline__ unsigned long long reduce_add_wide(uint32_t peers, uint32_t v) {
-    const uint32_t hi = __reduce_add_sync(peers, v >> 16);
-    const uint32_t lo = __reduce_add_sync(peers, v & 0xFFFFu);
-    return ((unsigned long long)hi << 16) + lo;
-}
-
-__global__ void __launch_bounds__(256) k_accumulate(Work w) {
-    const uint32_t nt = w.prob->ntiles;
-    const int lane = threadIdx.x & 31;
+// Features in (ToA, position) order, where a cluster's hits sit close
+// together: each pass over ACC_SPAN sorted positions sums into shared-memory
+// slots of the roots that lie inside the span (a root precedes all of its
+// cluster's hits), then adds one partial per such root to the global slots;
+// hits whose root lies before the span go straight to the global slots.
+// Sums of ToT*x and ToT*y are kept as 16-bit halves so 32-bit shared
+// atomics cannot overflow (span < 2^16 hits, ToT*x < 2^32).
+__global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
+    extern __shared__ uint32_t acc[];
+    uint32_t *a_size = acc, *a_tot = acc + ACC_SPAN, *a_wxh = acc + 2 * ACC_SPAN,
+             *a_wxl = acc + 3 * ACC_SPAN, *a_wyh = acc + 4 * ACC_SPAN, *a_wyl = acc + 5 * ACC_SPAN,
+             *a_min = acc + 6 * ACC_SPAN, *a_max = acc + 7 * ACC_SPAN;
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *sidx = w.vals[sorted_sel(P)];
+    const uint32_t *sroot = w.keys[sorted_sel(P) ^ 1u];   // written by k_flatten
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
-        const uint64_t base = g.toa_min;
-        for (uint32_t p0 = begin; p0 < end; p0 += blockDim.x) {
-            const uint32_t pos = p0 + threadIdx.x;
-            const bool valid = pos < end;
-            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            if (!valid) continue;
-            const uint32_t r = w.root_of[pos];
-            const uint4 v = ld_hit(g.hits + (pos - g.off));
-            const uint32_t tot = hit_tot(v), x = hit_x(v), y = hit_y(v);
-            const uint32_t key = (uint32_t)(hit_toa(v) - base);
-            const uint32_t peers = __match_any_sync(vmask, r);
-            const uint32_t sum_tot = __reduce_add_sync(peers, tot);
-            const unsigned long long wx = reduce_add_wide(peers, tot * x);
-            const unsigned long long wy = reduce_add_wide(peers, tot * y);
-            const uint32_t mn = __reduce_min_sync(peers, pos);
-            const uint32_t mx = __reduce_max_sync(peers, key);
-            if (lane == __ffs(peers) - 1) {
-                atomicAdd(&w.slot_size[r], (uint32_t)__popc(peers));
-                atomicAdd(&w.slot_tot[r], (unsigned long long)sum_tot);
-                atomicAdd(&w.slot_wx[r], wx);
-                atomicAdd(&w.slot_wy[r], wy);
-                atomicMin(&w.slot_min[r], mn);
-                atomicMax(&w.slot_maxkey[r], mx);
+        for (uint32_t b = begin; b < end; b += ACC_SPAN) {
+            const uint32_t e = b + ACC_SPAN < end ? b + ACC_SPAN : end;
+            uint32_t rr[ACC_ITEMS];
+#pragma unroll
+            for (int q = 0; q < ACC_ITEMS; ++q) {
+                const uint32_t s = b + q * ACC_THREADS + threadIdx.x;
+                rr[q] = s < e ? sroot[s] : 0;
             }
+#pragma unroll
+            for (int q = 0; q < ACC_ITEMS; ++q) {
+                const uint32_t k = q * ACC_THREADS + threadIdx.x;
+                if (b + k < e && rr[q] == b + k) {
+                    a_size[k] = a_tot[k] = a_wxh[k] = a_wxl[k] = a_wyh[k] = a_wyl[k] = 0;
+                    a_min[k] = 0xFFFFFFFFu;
+                    a_max[k] = 0;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < ACC_ITEMS; ++q) {
+                const uint32_t s = b + q * ACC_THREADS + threadIdx.x;
+                if (s >= e) continue;
+                const uint32_t r = rr[q];
+                const uint32_t pix = w.spix[s], tot = w.stot[s], key = skey[s], pos = sidx[s];
+                const uint32_t wx = tot * (pix & 0xFFFFu), wy = tot * (pix >> 16);
+                if (r >= b) {
+                    const uint32_t k = r - b;
+                    atomicAdd(&a_size[k], 1u);
+                    atomicAdd(&a_tot[k], tot);
+                    atomicAdd(&a_wxh[k], wx >> 16);
+                    atomicAdd(&a_wxl[k], wx & 0xFFFFu);
+                    atomicAdd(&a_wyh[k], wy >> 16);
+                    atomicAdd(&a_wyl[k], wy & 0xFFFFu);
+                    atomicMin(&a_min[k], pos);
+                    atomicMax(&a_max[k], key);
+                } else {
+                    atomicAdd(&w.slot_size[r], 1u);
+                    atomicAdd(&w.slot_tot[r], (unsigned long long)tot);
+                    atomicAdd(&w.slot_wx[r], (unsigned long long)wx);
+                    atomicAdd(&w.slot_wy[r], (unsigned long long)wy);
+                    atomicMin(&w.slot_min[r], pos);
+                    atomicMax(&w.slot_maxkey[r], key);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < ACC_ITEMS; ++q) {
+                const uint32_t k = q * ACC_THREADS + threadIdx.x;
+                const uint32_t r = b + k;
+                if (r < e && rr[q] == r) {
+                    atomicAdd(&w.slot_size[r], a_size[k]);
+                    atomicAdd(&w.slot_tot[r], (unsigned long long)a_tot[k]);
+                    atomicAdd(&w.slot_wx[r], ((unsigned long long)a_wxh[k] << 16) + a_wxl[k]);
+                    atomicAdd(&w.slot_wy[r], ((unsigned long long)a_wyh[k] << 16) + a_wyl[k]);
+                    atomicMin(&w.slot_min[r], a_min[k]);
+                    atomicMax(&w.slot_maxkey[r], a_max[k]);
+                }
+            }
+            __syncthreads();
         }
     }
 }
@@ -85,14 +125,27 @@ __global__ void __launch_bounds__(256) k_labels(Work w) {
         if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
         __syncthreads();
         uint32_t c_label = 0, c_closed = 0;
-        for (uint32_t p0 = begin; p0 < end; p0 += blockDim.x) {
-            const uint32_t pos = p0 + threadIdx.x;
+        constexpr int ITEMS = TILE / 256;
+        uint32_t rr[ITEMS], ll[ITEMS], mk[ITEMS];
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t pos = begin + q * 256 + threadIdx.x;
+            rr[q] = pos < end ? w.root_of[pos] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t pos = begin + q * 256 + threadIdx.x;
+            ll[q] = pos < end ? w.slot_min[rr[q]] : 0;
+            mk[q] = pos < end && g.close_mode == CLOSE_WM ? w.slot_maxkey[rr[q]] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t pos = begin + q * 256 + threadIdx.x;
             const bool valid = pos < end;
             bool is_label = false, closed = false;
             if (valid) {
-                const uint32_t r = w.root_of[pos];
-                const uint32_t l = w.slot_min[r];
-                closed = cluster_closed(g, w.slot_maxkey[r]);
+                const uint32_t l = ll[q];
+                closed = cluster_closed(g, mk[q]);
                 is_label = closed && l == pos;
                 const uint64_t lab = gidx_of(g, l - g.off);
                 if (direct) g.out_labels[pos - g.off] = lab;
@@ -272,16 +325,26 @@ __global__ void k_stream_end(Work w) {
     }
 }
 
+cudaError_t init_features_attributes() {
+    return cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, ACC_SMEM);
+}
+
 void launch_features(const Work &w, const Launch &L) {
-    k_accumulate<<<L.grid, 256, 0, L.stream>>>(w);
+    k_accumulate<<<L.grid, ACC_THREADS, ACC_SMEM, L.stream>>>(w);
+    L.mark("k_accumulate");
 }
 
 void launch_outputs(const Work &w, const Launch &L) {
     k_labels<<<L.grid, 256, 0, L.stream>>>(w);
+    L.mark("k_labels");
     k_tile_scan<<<MAX_SEGS, 1024, 0, L.stream>>>(w);
+    L.mark("k_tile_scan");
     k_records<<<L.grid, TILE_WORDS, 0, L.stream>>>(w);
+    L.mark("k_records");
     k_stream_compact<<<L.grid, TILE_WORDS, 0, L.stream>>>(w);
+    L.mark("k_stream_compact");
     k_stream_end<<<1, 256, 0, L.stream>>>(w);
+    L.mark("k_stream_end");
 }
 
 }  // namespace tpc

@@ -1,27 +1,30 @@
 // Neighbour search and union-find hooking (Algorithm 3 steps 4-5, Section 4.1)
 // for the edge-connectivity variant (iii)(a).
 //
-// Hits are in (ToA, position) order.  For hit i and each of its 9 pixels p
-// (8 neighbours plus its own), let L(i, p) be the latest earlier hit on p.
-// Joining i to L(i, p) whenever toa(i) - toa(L) <= dt yields the same
-// components as joining every pair within dt: an earlier hit j on p with
-// toa(i) - toa(j) <= dt reaches L(i, p) through the chain of consecutive
-// hits on p, all of which lie between toa(j) and toa(i) and are therefore
-// joined to one another.  This is the paper's "reference to the last hit at
-// each pixel" (Algorithm 3 step 4) made data parallel.
+// Hits are in (ToA, position) order ("rank" order).  Every edge (j, i) of
+// the hit graph — 8-adjacent or same pixel, |dToA| <= dt — has its earlier
+// end j among the hits within dt before i, so each hit looks only at that
+// time window and joins every adjacent hit in it (the complete edge set, so
+// the components are exact by construction).
 //
-// k_tile_link: one CTA per tile of TILE sorted hits.  The tile's pixels are
-// staged in shared memory as packed keys (pixel << 12 | rank), sorted, and
-// L(i, p) inside the tile is a binary search for the predecessor of
-// (p, rank(i)).  Unions run on a shared-memory forest and the tile's roots
-// are written to the global forest (roots = earliest hit).
+// k_tile_link: one CTA per tile of TILE ranks, staged in shared memory.
+//   window mode (sparse tiles: few hits within dt of a hit, on average):
+//     every pair (k, j < k) within dt is checked for adjacency, the pairs
+//     spread evenly over the threads by a prefix sum of the window lengths.
+//   bucket mode (dense tiles): the tile is counting-sorted into buckets of
+//     4x4-pixel cells (hashed onto NBUCKETS buckets) — the role of the
+//     paper's per-pixel reference matrix (Algorithm 3 step 4), sized to the
+//     tile instead of the sensor — and hit k scans the (at most four) buckets
+//     covering its 3x3 neighbourhood.
+//   Unions run on a shared-memory forest; the smallest rank of each
+//   component (its earliest hit) becomes the tile root in the global forest.
 //
 // k_border_link: edges whose earlier end lies before the tile (the paper's
 // step 5, "border hits at the start of the next chunk").  The halo is every
 // earlier hit within dt of the tile's first hit; the front is every tile hit
-// within dt of the halo's last hit.  The latest halo hit on each pixel is
-// found in a shared-memory sorted copy of the halo, processed in batches when
-// the halo is large; unions run on the global forest.
+// within dt of the halo's last hit.  Small borders are scanned pairwise
+// (ToA-ordered, stopping at dt); large ones bucket the halo by cell in shared
+// memory, in batches.  Unions run on the global forest.
 //
 // k_flatten: full path compression; records each position's root and
 // initialises the per-root feature slots.
@@ -30,46 +33,209 @@
 namespace tpc {
 
 constexpr int LINK_THREADS = 512;
-constexpr int LINK_RANK_BITS = 12;            // TILE = 4096 ranks
+constexpr int NBUCKETS = 2048;                // hashed 4x4-pixel cells
 constexpr int HALO_BATCH = 2048;
-constexpr int HALO_RANK_BITS = 11;
 constexpr int BORDER_THREADS = 256;
+constexpr uint32_t BORDER_PAIRS_DIRECT = 1u << 12;
 
-static_assert((1 << LINK_RANK_BITS) == TILE, "tile rank bits");
+__device__ __forceinline__ bool adjacent(uint32_t a, uint32_t b) {
+    const int dx = (int)(a & 0xFFFFu) - (int)(b & 0xFFFFu);
+    const int dy = (int)(a >> 16) - (int)(b >> 16);
+    return dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
+}
 
-// In-place ascending bitonic sort of n (power of two) 32-bit keys.
-__device__ __forceinline__ void bitonic_sort(uint32_t *v, uint32_t n) {
-    for (uint32_t k = 2; k <= n; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint32_t a = v[i], b = v[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) { v[i] = b; v[ixj] = a; }
-                }
-            }
-            __syncthreads();
-        }
+// Shared-memory forest with randomised linking: the root with the lower
+// pseudo-random priority is hooked under the other, which keeps the expected
+// tree depth logarithmic however the edges arrive (linking by index would
+// chain a 300-hit track whose edges are joined in parallel).  The smallest
+// rank of each component is found afterwards.
+__device__ __forceinline__ uint32_t link_prio(uint32_t k) {
+    uint32_t h = k * 0x9E3779B1u;
+    h ^= h >> 15;
+    h *= 0x85EBCA77u;
+    return h ^ (h >> 13);
+}
+
+__device__ __forceinline__ void sunion_prio(uint32_t *parent, uint32_t a, uint32_t b) {
+    while (true) {
+        a = sfind(parent, a);
+        b = sfind(parent, b);
+        if (a == b) return;
+        const uint32_t pa = link_prio(a), pb = link_prio(b);
+        if (pa < pb || (pa == pb && a < b)) { uint32_t t = a; a = b; b = t; }
+        // b has the lower priority: hook it under a
+        if (atomicCAS(parent + b, b, a) == b) return;
     }
 }
 
-// Number of entries of the ascending array v[0..n) that are < target (n a
-// power of two).
-__device__ __forceinline__ uint32_t count_less(const uint32_t *v, uint32_t n, uint32_t target) {
-    uint32_t pos = 0;
-    for (uint32_t step = n >> 1; step > 0; step >>= 1)
-        if (v[pos + step - 1] < target) pos += step;
-    if (v[pos] < target) pos += 1;
-    return pos;
+// Bucket of the 4x4-pixel cell holding (x, y); cells are hashed onto
+// NBUCKETS buckets (a collision only adds candidates, never drops one).
+__device__ __forceinline__ uint32_t cell_bucket(uint32_t x, uint32_t y, uint32_t cw) {
+    return ((y >> 2) * cw + (x >> 2)) & (NBUCKETS - 1);
+}
+
+// The (up to four) distinct buckets covering the 3x3 neighbourhood of (x, y).
+__device__ __forceinline__ int neighbour_buckets(uint32_t pix, uint32_t W, uint32_t H, uint32_t cw,
+                                                 uint32_t b[4]) {
+    const uint32_t x = pix & 0xFFFFu, y = pix >> 16;
+    const uint32_t x0 = x ? x - 1 : 0, x1 = x + 1 < W ? x + 1 : x;
+    const uint32_t y0 = y ? y - 1 : 0, y1 = y + 1 < H ? y + 1 : y;
+    int n = 0;
+    const uint32_t cand[4] = {cell_bucket(x0, y0, cw), cell_bucket(x1, y0, cw),
+                              cell_bucket(x0, y1, cw), cell_bucket(x1, y1, cw)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        bool dup = false;
+        for (int j = 0; j < n; ++j) dup |= b[j] == cand[i];
+        if (!dup) b[n++] = cand[i];
+    }
+    return n;
+}
+
+// Counting sort of entries 0..n of s_pix into cell buckets: bucket q holds
+// s_seg[s_start[q] .. s_start[q+1]).  Order inside a bucket is arbitrary
+// (the scans below compare ranks explicitly).
+__device__ void bucket_sort(const uint32_t *s_pix, uint32_t n, uint32_t cw, uint32_t *s_start,
+                            uint32_t *s_cur, uint16_t *s_seg, uint32_t *s_warp) {
+    for (uint32_t q = threadIdx.x; q <= NBUCKETS; q += blockDim.x) s_start[q] = 0;
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
+        atomicAdd(&s_start[cell_bucket(s_pix[k] & 0xFFFFu, s_pix[k] >> 16, cw) + 1], 1u);
+    __syncthreads();
+    // inclusive scan of s_start[1..NBUCKETS]: each thread owns `per` consecutive entries
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (NBUCKETS + blockDim.x - 1) / blockDim.x;
+    const uint32_t i0 = 1 + threadIdx.x * per;
+    uint32_t local = 0;
+    for (uint32_t i = i0; i < i0 + per && i <= NBUCKETS; ++i) local += s_start[i];
+    uint32_t x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t run = x - local;
+    for (int q = 0; q < warp; ++q) run += s_warp[q];
+    __syncthreads();
+    for (uint32_t i = i0; i < i0 + per && i <= NBUCKETS; ++i) {
+        run += s_start[i];
+        s_start[i] = run;
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < NBUCKETS; q += blockDim.x) s_cur[q] = s_start[q];
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const uint32_t q = cell_bucket(s_pix[k] & 0xFFFFu, s_pix[k] >> 16, cw);
+        s_seg[atomicAdd(&s_cur[q], 1u)] = (uint16_t)k;
+    }
+    __syncthreads();
+}
+
+// Load-balanced window scan: every pair (k, j) with j < k and
+// key(k) - key(j) <= dt is one unit of work; a prefix sum over the window
+// lengths hands each thread an equal slice of the pairs, so lanes neither
+// wait on long windows (bursty tracks) nor on each other.
+constexpr uint32_t EDGE_BUF = 256;   // queued adjacent pairs per warp
+
+__device__ void link_window(const uint32_t *s_key, const uint32_t *s_pix, uint32_t *s_par,
+                            uint16_t *s_lo, uint32_t *s_pref, uint32_t *s_warp, uint32_t *s_edges,
+                            uint32_t n_t, uint32_t dt) {
+    constexpr uint32_t PER = TILE / LINK_THREADS;
+    const uint32_t k0 = threadIdx.x * PER;
+    uint32_t sum = 0;
+    if (k0 < n_t) {
+        const uint32_t key0 = s_key[k0], tgt = key0 >= dt ? key0 - dt : 0;
+        uint32_t lo = 0, hi = k0;           // first rank with key >= tgt
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_key[mid] < tgt) lo = mid + 1; else hi = mid;
+        }
+        for (uint32_t k = k0; k < k0 + PER && k < n_t; ++k) {
+            const uint32_t key = s_key[k];
+            while (key - s_key[lo] > dt) ++lo;
+            s_lo[k] = (uint16_t)lo;
+            sum += k - lo;
+        }
+    }
+    // exclusive prefix of the window lengths: s_pref[k], s_pref[n_t] = total
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t run = x - sum;
+    for (int q = 0; q < warp; ++q) run += s_warp[q];
+    for (uint32_t k = k0; k < k0 + PER && k < n_t; ++k) {
+        s_pref[k] = run;
+        run += k - s_lo[k];
+    }
+    if (threadIdx.x == LINK_THREADS - 1) {
+        uint32_t tot = 0;
+        for (int q = 0; q < LINK_THREADS / 32; ++q) tot += s_warp[q];
+        s_pref[n_t] = tot;
+    }
+    __syncthreads();
+    const uint32_t total = s_pref[n_t];
+    // each warp takes a contiguous range of pairs; lane i handles pair
+    // base + i, so lanes share the hit k (broadcast reads) and read
+    // consecutive earlier hits j (no bank conflicts)
+    constexpr uint32_t NW = LINK_THREADS / 32;
+    const uint32_t w0 = (uint32_t)((uint64_t)total * warp / NW);
+    const uint32_t w1 = (uint32_t)((uint64_t)total * (warp + 1) / NW);
+    uint32_t k = 0;
+    if (w0 + lane < w1) {
+        uint32_t lo = 0, hi = n_t;          // last k with s_pref[k] <= p
+        const uint32_t p = w0 + lane;
+        while (lo + 1 < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_pref[mid] <= p) lo = mid; else hi = mid;
+        }
+        k = lo;
+    }
+    // adjacent pairs are queued per warp and joined by all 32 lanes at once
+    // (a round has only a few adjacent pairs; joining them where they are
+    // found would leave most lanes idle behind a latency-bound union)
+    uint32_t *buf = s_edges + warp * EDGE_BUF;
+    uint32_t count = 0;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t pb = w0; pb < w1; pb += 32) {
+        const uint32_t p = pb + lane;
+        bool adj = false;
+        uint32_t j = 0;
+        if (p < w1) {
+            while (p >= s_pref[k + 1]) ++k;
+            j = s_lo[k] + (p - s_pref[k]);
+            adj = adjacent(s_pix[k], s_pix[j]);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, adj);
+        if (adj) buf[count + __popc(m & lt)] = (k << 16) | j;
+        count += __popc(m);
+        if (count > EDGE_BUF - 32) {
+            __syncwarp();
+            for (uint32_t i = lane; i < count; i += 32) sunion_prio(s_par, buf[i] >> 16, buf[i] & 0xFFFFu);
+            __syncwarp();
+            count = 0;
+        }
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < count; i += 32) sunion_prio(s_par, buf[i] >> 16, buf[i] & 0xFFFFu);
 }
 
 __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
     extern __shared__ uint32_t smem[];
-    uint32_t *s_key = smem;             // [TILE] keys of the tile (rank order)
-    uint32_t *s_pix = s_key + TILE;     // [TILE] x | y << 16
-    uint32_t *s_v = s_pix + TILE;       // [TILE] pixel << 12 | rank, sorted
-    uint32_t *s_par = s_v + TILE;       // [TILE] shared-memory forest
+    uint32_t *s_key = smem;                  // [TILE]
+    uint32_t *s_pix = s_key + TILE;          // [TILE] x | y << 16
+    uint32_t *s_par = s_pix + TILE;          // [TILE] shared-memory forest
+    uint32_t *s_start = s_par + TILE;        // [NBUCKETS + 1] (window mode: prefix, TILE + 1)
+    uint32_t *s_cur = s_start + NBUCKETS + 1;  // [NBUCKETS]
+    uint32_t *s_warp = s_cur + NBUCKETS;     // [32]
+    uint16_t *s_seg = reinterpret_cast<uint16_t *>(s_warp + 32);  // [TILE] (window mode: lo)
+    uint32_t *s_edges = reinterpret_cast<uint32_t *>(s_seg + TILE);  // [warps * EDGE_BUF]
+    static_assert(2 * NBUCKETS + 1 >= TILE + 1, "prefix array size");
 
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
@@ -79,49 +245,61 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         const uint32_t n_t = end - begin, W = g.width, H = g.height, dt = g.dt;
-        for (uint32_t k = threadIdx.x; k < TILE; k += LINK_THREADS) {
-            if (k < n_t) {
-                const uint32_t pix = w.spix[begin + k];
-                const uint32_t pid = (pix >> 16) * W + (pix & 0xFFFFu);
-                s_key[k] = skey[begin + k];
-                s_pix[k] = pix;
-                s_v[k] = (pid << LINK_RANK_BITS) | k;
-            } else {
-                s_v[k] = 0xFFFFFFFFu;
-            }
+        const uint32_t cw = (W + 3) >> 2;
+        for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS) {
+            s_key[k] = skey[begin + k];
+            s_pix[k] = w.spix[begin + k];
             s_par[k] = k;
         }
         __syncthreads();
-        bitonic_sort(s_v, TILE);
-        for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS) {
-            const uint32_t pix = s_pix[k], key = s_key[k];
-            const int x = (int)(pix & 0xFFFFu), y = (int)(pix >> 16);
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int ny = y + dy;
-                if (ny < 0 || ny >= (int)H) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int nx = x + dx;
-                    if (nx < 0 || nx >= (int)W) continue;
-                    const uint32_t p = (uint32_t)ny * W + (uint32_t)nx;
-                    const uint32_t c = count_less(s_v, TILE, (p << LINK_RANK_BITS) | k);
-                    if (c == 0) continue;
-                    const uint32_t e = s_v[c - 1];
-                    if ((e >> LINK_RANK_BITS) != p) continue;
-                    const uint32_t j = e & (TILE - 1);
-                    if (key - s_key[j] <= dt) sunion(s_par, k, j);
+        // mean window length (hits within dt before a hit) decides the mode
+        const uint64_t span = (uint64_t)(s_key[n_t - 1] - s_key[0]) + 1;
+        const uint64_t window = (uint64_t)n_t * ((uint64_t)dt + 1) / span;
+        if (window <= 48) {
+            link_window(s_key, s_pix, s_par, s_seg, s_start, s_warp, s_edges, n_t, dt);
+        } else {
+            bucket_sort(s_pix, n_t, cw, s_start, s_cur, s_seg, s_warp);
+            for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS) {
+                const uint32_t key = s_key[k], pix = s_pix[k];
+                uint32_t b[4];
+                const int nb = neighbour_buckets(pix, W, H, cw, b);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (i >= nb) break;
+                    for (uint32_t q = s_start[b[i]]; q < s_start[b[i] + 1]; ++q) {
+                        const uint32_t j = s_seg[q];
+                        if (j < k && key - s_key[j] <= dt && adjacent(pix, s_pix[j])) sunion_prio(s_par, k, j);
+                    }
                 }
             }
         }
         __syncthreads();
+        // smallest rank per component; the bucket arrays are free again
+        // (s_start and s_cur are contiguous: 2 * NBUCKETS + 1 >= TILE entries)
+        static_assert(2 * NBUCKETS + 1 >= TILE, "min array size");
+        uint32_t *s_min = s_start;
+        for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS) s_min[k] = 0xFFFFFFFFu;
+        __syncthreads();
+        uint32_t *s_root = s_key;   // keys are no longer needed; only k's thread writes s_root[k]
+        for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS) {
+            const uint32_t r = sfind(s_par, k);
+            s_root[k] = r;
+            atomicMin(&s_min[r], k);
+        }
+        __syncthreads();
         for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS)
-            w.parent[begin + k] = begin + sfind(s_par, k);
+            w.parent[begin + k] = begin + s_min[s_root[k]];
         __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
-    __shared__ uint32_t b_v[HALO_BATCH];
     __shared__ uint32_t b_key[HALO_BATCH];
+    __shared__ uint32_t b_pix[HALO_BATCH];
+    __shared__ uint32_t b_start[NBUCKETS + 1];
+    __shared__ uint32_t b_cur[NBUCKETS];
+    __shared__ uint32_t b_warp[32];
+    __shared__ uint16_t b_seg[HALO_BATCH];
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
@@ -130,7 +308,7 @@ __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
         if (t == g.tile0) continue;   // nothing before the segment's first tile
         uint32_t s0, end;
         tile_range(g, t, s0, end);
-        const uint32_t W = g.width, H = g.height, dt = g.dt;
+        const uint32_t W = g.width, H = g.height, dt = g.dt, cw = (W + 3) >> 2;
         // halo: [h0, s0) = earlier hits with key >= key(s0) - dt (a suffix)
         const uint32_t k0 = skey[s0];
         const uint32_t lo_key = k0 >= dt ? k0 - dt : 0;
@@ -156,39 +334,34 @@ __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
             e0 += cnt;
             if (cnt < chunk) break;
         }
-        for (uint32_t hb = h0; hb < s0; hb += HALO_BATCH) {
-            const uint32_t nb = s0 - hb < HALO_BATCH ? s0 - hb : HALO_BATCH;
-            uint32_t np2 = 2;
-            while (np2 < nb) np2 <<= 1;
-            for (uint32_t j = threadIdx.x; j < np2; j += BORDER_THREADS) {
-                if (j < nb) {
-                    const uint32_t pix = w.spix[hb + j];
-                    const uint32_t pid = (pix >> 16) * W + (pix & 0xFFFFu);
-                    b_v[j] = (pid << HALO_RANK_BITS) | j;
-                    b_key[j] = skey[hb + j];
-                } else {
-                    b_v[j] = 0xFFFFFFFFu;
+        const uint32_t nh = s0 - h0, nf = e0 - s0;
+        if (nh * (uint64_t)nf <= BORDER_PAIRS_DIRECT) {
+            // every (front, halo) pair within dt, newest halo hit first
+            for (uint32_t i = s0 + threadIdx.x; i < e0; i += BORDER_THREADS) {
+                const uint32_t key = skey[i], pix = w.spix[i];
+                for (uint32_t j = s0; j-- > h0;) {
+                    if (key - skey[j] > dt) break;
+                    if (adjacent(pix, w.spix[j])) gunion(w.parent, i, j);
                 }
             }
+            continue;
+        }
+        for (uint32_t hb = h0; hb < s0; hb += HALO_BATCH) {
+            const uint32_t n_b = s0 - hb < HALO_BATCH ? s0 - hb : HALO_BATCH;
+            for (uint32_t j = threadIdx.x; j < n_b; j += BORDER_THREADS) {
+                b_key[j] = skey[hb + j];
+                b_pix[j] = w.spix[hb + j];
+            }
             __syncthreads();
-            bitonic_sort(b_v, np2);
+            bucket_sort(b_pix, n_b, cw, b_start, b_cur, b_seg, b_warp);
             for (uint32_t i = s0 + threadIdx.x; i < e0; i += BORDER_THREADS) {
-                const uint32_t pix = w.spix[i], key = skey[i];
-                const int x = (int)(pix & 0xFFFFu), y = (int)(pix >> 16);
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int ny = y + dy;
-                    if (ny < 0 || ny >= (int)H) continue;
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int nx = x + dx;
-                        if (nx < 0 || nx >= (int)W) continue;
-                        const uint32_t p = (uint32_t)ny * W + (uint32_t)nx;
-                        // latest halo hit on p: the largest entry below (p + 1) << bits
-                        const uint32_t c = count_less(b_v, np2, (p + 1) << HALO_RANK_BITS);
-                        if (c == 0) continue;
-                        const uint32_t e = b_v[c - 1];
-                        if ((e >> HALO_RANK_BITS) != p) continue;
-                        const uint32_t j = e & (HALO_BATCH - 1);
-                        if (key - b_key[j] <= dt) gunion(w.parent, i, hb + j);
+                const uint32_t key = skey[i], pix = w.spix[i];
+                uint32_t b[4];
+                const int nb = neighbour_buckets(pix, W, H, cw, b);
+                for (int q2 = 0; q2 < nb; ++q2) {
+                    for (uint32_t q = b_start[b[q2]]; q < b_start[b[q2] + 1]; ++q) {
+                        const uint32_t j = b_seg[q];
+                        if (key - b_key[j] <= dt && adjacent(pix, b_pix[j])) gunion(w.parent, i, hb + j);
                     }
                 }
             }
@@ -201,13 +374,29 @@ __global__ void __launch_bounds__(256) k_flatten(Work w) {
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
     const uint32_t *sidx = w.vals[sorted_sel(P)];
+    uint32_t *sroot = w.keys[sorted_sel(P) ^ 1u];
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
-        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
-            const uint32_t r = gfind(w.parent, s);
-            w.root_of[sidx[s]] = r;
+        constexpr int ITEMS = TILE / 256;
+        uint32_t par[ITEMS], pos[ITEMS];
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t s = begin + q * 256 + threadIdx.x;
+            par[q] = s < end ? w.parent[s] : 0;
+            pos[q] = s < end ? sidx[s] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t s = begin + q * 256 + threadIdx.x;
+            if (s >= end) continue;
+            const uint32_t r = par[q] == s ? s : gfind(w.parent, par[q]);
+            // the idle radix buffer receives each sorted position's root: only
+            // this thread writes it (parent[] itself may still be rewritten by
+            // other threads' path halving with a stale ancestor)
+            sroot[s] = r;
+            w.root_of[pos[q]] = r;
             if (r == s) {
                 w.slot_size[r] = 0;
                 w.slot_min[r] = 0xFFFFFFFFu;
@@ -220,17 +409,25 @@ __global__ void __launch_bounds__(256) k_flatten(Work w) {
     }
 }
 
-constexpr int TILE_LINK_SMEM = 4 * TILE * (int)sizeof(uint32_t);
+constexpr int TILE_LINK_SMEM = (3 * TILE + 2 * NBUCKETS + 1 + 32) * (int)sizeof(uint32_t) +
+                               TILE * (int)sizeof(uint16_t) +
+                               (LINK_THREADS / 32) * EDGE_BUF * (int)sizeof(uint32_t);
+
+cudaError_t init_features_attributes();
 
 cudaError_t init_kernel_attributes() {
-    return cudaFuncSetAttribute(k_tile_link, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_LINK_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_tile_link, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_LINK_SMEM);
+    return e == cudaSuccess ? init_features_attributes() : e;
 }
 
 void launch_link(const Work &w, const Launch &L) {
     const int smem = TILE_LINK_SMEM;
     k_tile_link<<<L.grid, LINK_THREADS, smem, L.stream>>>(w);
+    L.mark("k_tile_link");
     k_border_link<<<L.grid, BORDER_THREADS, 0, L.stream>>>(w);
+    L.mark("k_border_link");
     k_flatten<<<L.grid, 256, 0, L.stream>>>(w);
+    L.mark("k_flatten");
 }
 
 }  // namespace tpc

@@ -92,14 +92,25 @@ __global__ void __launch_bounds__(256) k_prepare(Work w) {
         const uint32_t off = g.off, W = g.width, H = g.height, nc = g.n_carry;
         uint64_t mn = ~0ull, mx = 0, cmn = ~0ull;
         bool bad = false;
-        for (uint32_t pos = begin + threadIdx.x; pos < end; pos += blockDim.x) {
-            const uint32_t j = pos - off;
-            uint4 v = ld_hit(hits + j);
-            bad |= hit_x(v) >= W || hit_y(v) >= H;
-            uint64_t toa = hit_toa(v);
-            mn = toa < mn ? toa : mn;
-            mx = toa > mx ? toa : mx;
-            if (j >= nc) cmn = toa < cmn ? toa : cmn;
+        constexpr int U = 4;
+        for (uint32_t p0 = begin + threadIdx.x; p0 < end; p0 += U * blockDim.x) {
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t pos = p0 + u * blockDim.x;
+                if (pos < end) v[u] = ld_hit(hits + (pos - off));
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t pos = p0 + u * blockDim.x;
+                if (pos >= end) continue;
+                const uint32_t j = pos - off;
+                bad |= hit_x(v[u]) >= W || hit_y(v[u]) >= H;
+                const uint64_t toa = hit_toa(v[u]);
+                mn = toa < mn ? toa : mn;
+                mx = toa > mx ? toa : mx;
+                if (j >= nc) cmn = toa < cmn ? toa : cmn;
+            }
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&w.prob->err, E_RANGE);
         mn = warp_min_u64(mn);
@@ -175,15 +186,27 @@ __global__ void __launch_bounds__(256) k_make_keys(Work w) {
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         const uint64_t base = g.toa_min;
-        for (uint32_t pos = begin + threadIdx.x; pos < end; pos += blockDim.x) {
-            uint4 v = ld_hit(g.hits + (pos - g.off));
-            w.keys[0][pos] = (uint32_t)(hit_toa(v) - base);
-            w.vals[0][pos] = pos;
+        constexpr int U = 4;
+        for (uint32_t p0 = begin + threadIdx.x; p0 < end; p0 += U * blockDim.x) {
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t pos = p0 + u * blockDim.x;
+                if (pos < end) v[u] = ld_hit(g.hits + (pos - g.off));
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t pos = p0 + u * blockDim.x;
+                if (pos < end) {
+                    w.keys[0][pos] = (uint32_t)(hit_toa(v[u]) - base);
+                    w.vals[0][pos] = pos;
+                }
+            }
         }
     }
 }
 
-// spix[s] = pixel of the hit at sorted position s.
+// spix[s], stot[s] = pixel and ToT of the hit at sorted position s.
 __global__ void __launch_bounds__(256) k_gather(Work w) {
     const uint32_t nt = w.prob->ntiles;
     const uint32_t *vals = w.vals[sorted_sel(*w.prob)];
@@ -191,27 +214,49 @@ __global__ void __launch_bounds__(256) k_gather(Work w) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
-        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
-            uint4 v = ld_hit(g.hits + (vals[s] - g.off));
-            w.spix[s] = v.x;   // x | y << 16
+        constexpr int ITEMS = TILE / 256;
+        uint32_t pv[ITEMS];
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t s = begin + r * 256 + threadIdx.x;
+            pv[r] = s < end ? vals[s] : 0;
+        }
+        uint2 px[ITEMS];
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t s = begin + r * 256 + threadIdx.x;
+            px[r] = s < end ? __ldg(reinterpret_cast<const uint2 *>(g.hits + (pv[r] - g.off))) : make_uint2(0, 0);
+        }
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t s = begin + r * 256 + threadIdx.x;
+            if (s < end) {
+                w.spix[s] = px[r].x;                     // x | y << 16
+                w.stot[s] = (uint16_t)(px[r].y & 0xFFFFu);
+            }
         }
     }
 }
 
-void launch_setup(const Work &w, int nsegs, cudaStream_t st) {
-    k_setup<<<1, 1024, 0, st>>>(w, nsegs);
+void launch_setup(const Work &w, int nsegs, const Launch &L) {
+    k_setup<<<1, 1024, 0, L.stream>>>(w, nsegs);
+    L.mark("k_setup");
 }
 void launch_prepare(const Work &w, const Launch &L) {
     k_prepare<<<L.grid, 256, 0, L.stream>>>(w);
+    L.mark("k_prepare");
 }
-void launch_seg_finalize(const Work &w, cudaStream_t st) {
-    k_seg_finalize<<<1, 256, 0, st>>>(w);
+void launch_seg_finalize(const Work &w, const Launch &L) {
+    k_seg_finalize<<<1, 256, 0, L.stream>>>(w);
+    L.mark("k_seg_finalize");
 }
 void launch_make_keys(const Work &w, const Launch &L) {
     k_make_keys<<<L.grid, 256, 0, L.stream>>>(w);
+    L.mark("k_make_keys");
 }
 void launch_gather(const Work &w, const Launch &L) {
     k_gather<<<L.grid, 256, 0, L.stream>>>(w);
+    L.mark("k_gather");
 }
 
 }  // namespace tpc

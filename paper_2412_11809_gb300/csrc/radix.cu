@@ -20,6 +20,19 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Lanes of `vmask` holding the same 8-bit digit as this lane, from eight
+// ballots (cheaper than match.any on this hardware).
+__device__ __forceinline__ uint32_t match_digit(uint32_t d, uint32_t vmask) {
+    uint32_t peers = vmask;
+#pragma unroll
+    for (int b = 0; b < RADIX_BITS; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 // Exclusive scan of one value per thread over a CTA of NT threads.
 template <int NT>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp, uint32_t &total) {
@@ -52,21 +65,27 @@ __global__ void __launch_bounds__(256) k_radix_upsweep(Work w, int pass) {
     const uint32_t nt = w.prob->ntiles, cap = w.prob->tile_cap;
     const uint32_t *keys = w.keys[pass & 1];
     const int shift = pass * RADIX_BITS;
+    constexpr int ITEMS = TILE / 256;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
+        uint32_t kk[ITEMS];
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {   // all loads in flight before any use
+            const uint32_t pos = begin + r * 256 + threadIdx.x;
+            kk[r] = pos < end ? keys[pos] : 0;
+        }
         cnt[threadIdx.x] = 0;
         __syncthreads();
-        for (uint32_t p0 = begin; p0 < end; p0 += blockDim.x) {
-            const uint32_t pos = p0 + threadIdx.x;
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t pos = begin + r * 256 + threadIdx.x;
             const bool valid = pos < end;
             const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            if (valid) {
-                const uint32_t d = (keys[pos] >> shift) & (RADIX - 1);
-                const uint32_t peers = __match_any_sync(vmask, d);
-                if ((peers & lanemask_lt()) == 0) atomicAdd(&cnt[d], __popc(peers));
-            }
+            const uint32_t d = (kk[r] >> shift) & (RADIX - 1);
+            const uint32_t peers = match_digit(d, vmask);
+            if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[d], __popc(peers));
         }
         __syncthreads();
         w.hist[threadIdx.x * cap + t] = cnt[threadIdx.x];
@@ -126,23 +145,26 @@ __global__ void __launch_bounds__(DS_THREADS) k_radix_downsweep(Work w, int pass
 
         uint32_t kk[DS_ITEMS], vv[DS_ITEMS], rr[DS_ITEMS];
 #pragma unroll
+        for (int r = 0; r < DS_ITEMS; ++r) {   // all loads in flight before the ranking
+            const uint32_t idx = warp * DS_WARP_SPAN + r * 32 + lane;
+            kk[r] = idx < n_t ? keys_in[begin + idx] : 0;
+            vv[r] = idx < n_t ? vals_in[begin + idx] : 0;
+        }
+#pragma unroll
         for (int r = 0; r < DS_ITEMS; ++r) {
             const uint32_t idx = warp * DS_WARP_SPAN + r * 32 + lane;
             const bool valid = idx < n_t;
             const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            uint32_t key = 0, d = 0, pre = 0, rank = 0, peers = 0;
+            const uint32_t key = kk[r], d = (key >> shift) & (RADIX - 1);
+            const uint32_t peers = match_digit(d, vmask);
+            uint32_t pre = 0, rank = 0;
             if (valid) {
-                key = keys_in[begin + idx];
-                vv[r] = vals_in[begin + idx];
-                d = (key >> shift) & (RADIX - 1);
-                peers = __match_any_sync(vmask, d);
                 rank = __popc(peers & lt);
                 pre = s_wcnt[warp][d];
             }
             __syncwarp();
             if (valid && rank == 0) s_wcnt[warp][d] = pre + __popc(peers);
             __syncwarp();
-            kk[r] = key;
             rr[r] = pre + rank;
         }
         __syncthreads();
@@ -182,9 +204,16 @@ __global__ void __launch_bounds__(DS_THREADS) k_radix_downsweep(Work w, int pass
 }
 
 void launch_radix_pass(const Work &w, int pass, const Launch &L) {
+    static const char *up[4] = {"k_radix_upsweep0", "k_radix_upsweep1", "k_radix_upsweep2", "k_radix_upsweep3"};
+    static const char *sc[4] = {"k_radix_scan0", "k_radix_scan1", "k_radix_scan2", "k_radix_scan3"};
+    static const char *dn[4] = {"k_radix_downsweep0", "k_radix_downsweep1", "k_radix_downsweep2",
+                                "k_radix_downsweep3"};
     k_radix_upsweep<<<L.grid, 256, 0, L.stream>>>(w, pass);
+    L.mark(up[pass & 3]);
     k_radix_scan<<<RADIX, 1024, 0, L.stream>>>(w, pass);
+    L.mark(sc[pass & 3]);
     k_radix_downsweep<<<L.grid, DS_THREADS, 0, L.stream>>>(w, pass);
+    L.mark(dn[pass & 3]);
 }
 
 }  // namespace tpc

@@ -77,6 +77,7 @@ struct Workspace {
         w.vals[0] = mem.alloc<uint32_t>(P, e);
         w.vals[1] = mem.alloc<uint32_t>(P, e);
         w.spix = mem.alloc<uint32_t>(P, e);
+        w.stot = mem.alloc<uint16_t>(P, e);
         w.parent = mem.alloc<uint32_t>(P, e);
         w.root_of = mem.alloc<uint32_t>(P, e);
         w.slot_size = mem.alloc<uint32_t>(P, e);
@@ -234,9 +235,9 @@ cudaError_t upload_segs(tpc_ctx *c, const Work &w, const Seg *segs, int nsegs, c
 }
 
 void enqueue_kernels(const Work &w, int nsegs, const Launch &L) {
-    launch_setup(w, nsegs, L.stream);
+    launch_setup(w, nsegs, L);
     launch_prepare(w, L);
-    launch_seg_finalize(w, L.stream);
+    launch_seg_finalize(w, L);
     launch_make_keys(w, L);
     for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
     launch_gather(w, L);
@@ -247,8 +248,13 @@ void enqueue_kernels(const Work &w, int nsegs, const Launch &L) {
 
 // Run the fixed kernel sequence, from a CUDA graph captured on first use
 // (and re-captured when the workspace or the segment count changes).
-cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st) {
+cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, Tracer *tr = nullptr) {
     const Launch L{grid_of(owner), st};
+    if (tr) {   // kernels one by one with an event after each (no graph)
+        cudaEventRecord(tr->ev[0], st);
+        enqueue_kernels(ws.w, nsegs, Launch{L.grid, st, tr});
+        return cudaGetLastError();
+    }
     if (!owner->graph || owner->graph_nsegs != nsegs || owner->graph_pos_cap != ws.pos_cap ||
         owner->graph_grid != L.grid) {
         if (owner->graph) {
@@ -547,10 +553,9 @@ int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
     return TPC_OK;
 }
 
-int tpc_flush(tpc_ctx *c) {
-    if (!c) return TPC_ERR_ARG;
-    std::lock_guard<std::mutex> lk(c->mu);
+static int flush_impl(tpc_ctx *c, Tracer *tr) {
     if (c->max_disorder != ~0ull) {
+        if (tr) return TPC_ERR_STATE;
         int rc = ensure_stream_buffers(c, 0);
         if (rc) return rc;
         return stream_step(c, 0, true);
@@ -569,7 +574,7 @@ int tpc_flush(tpc_ctx *c) {
     s.gidx_base = c->pushed;
     s.n_new = (uint32_t)n;
     if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
-    if (run_step(c, c->ws, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (run_step(c, c->ws, 1, c->stream, tr) != cudaSuccess) return TPC_ERR_CUDA;
     c->res_base = c->pushed;
     c->pushed += n;
     c->pending = 0;
@@ -579,6 +584,35 @@ int tpc_flush(tpc_ctx *c) {
     c->has_result = true;
     c->res_streaming = false;
     return TPC_OK;
+}
+
+int tpc_flush(tpc_ctx *c) {
+    if (!c) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    return flush_impl(c, nullptr);
+}
+
+int tpc_profile_flush(tpc_ctx *c, const char **names, float *ms, int cap, int *n_out) {
+    if (!c || !n_out || cap < 0 || (cap && (!names || !ms))) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    Tracer tr;
+    for (int i = 0; i <= Tracer::MAX; ++i)
+        if (cudaEventCreate(&tr.ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(tr.ev[j]);
+            return TPC_ERR_CUDA;
+        }
+    int rc = flush_impl(c, &tr);
+    if (rc == TPC_OK && cudaEventSynchronize(tr.ev[tr.n]) != cudaSuccess) rc = TPC_ERR_CUDA;
+    if (rc == TPC_OK) {
+        *n_out = tr.n;
+        for (int i = 0; i < tr.n && i < cap; ++i) {
+            names[i] = tr.names[i];
+            cudaEventElapsedTime(&ms[i], tr.ev[i], tr.ev[i + 1]);
+        }
+        if (tr.n > cap) rc = TPC_ERR_CAP;
+    }
+    for (int i = 0; i <= Tracer::MAX; ++i) cudaEventDestroy(tr.ev[i]);
+    return rc;
 }
 
 int tpc_sync(tpc_ctx *c) {

@@ -18,7 +18,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/tpc.h"
+#include "tpc.h"
 
 namespace tpc {
 
@@ -102,6 +102,7 @@ struct Work {
     uint32_t *keys[2];         // radix ping-pong: ToA - toa_min
     uint32_t *vals[2];         // radix ping-pong: position
     uint32_t *spix;            // sorted positions: x | y << 16
+    uint16_t *stot;            // sorted positions: ToT
     uint32_t *parent;          // union-find over sorted positions
     uint32_t *root_of;         // per position: root (a sorted position)
     uint32_t *slot_size;       // per root
@@ -195,15 +196,31 @@ __device__ __forceinline__ uint64_t hit_toa(uint4 v) { return ((uint64_t)v.w << 
 // ---------------------------------------------------------------------------
 // host-side launchers (one translation unit each)
 
+// Optional per-kernel tracing: an event after every launch.
+struct Tracer {
+    static constexpr int MAX = 64;
+    cudaEvent_t ev[MAX + 1];
+    const char *names[MAX];
+    int n = 0;
+    void mark(const char *name, cudaStream_t st) {
+        if (n < MAX) {
+            names[n] = name;
+            cudaEventRecord(ev[++n], st);
+        }
+    }
+};
+
 struct Launch {
     int grid;          // persistent CTAs
     cudaStream_t stream;
+    Tracer *tr = nullptr;
+    void mark(const char *name) const { if (tr) tr->mark(name, stream); }
 };
 
 cudaError_t init_kernel_attributes();   // once per process and device, before capture
-void launch_setup(const Work &w, int nsegs, cudaStream_t st);
+void launch_setup(const Work &w, int nsegs, const Launch &L);
 void launch_prepare(const Work &w, const Launch &L);
-void launch_seg_finalize(const Work &w, cudaStream_t st);
+void launch_seg_finalize(const Work &w, const Launch &L);
 void launch_make_keys(const Work &w, const Launch &L);
 void launch_radix_pass(const Work &w, int pass, const Launch &L);
 void launch_gather(const Work &w, const Launch &L);
