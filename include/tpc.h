@@ -162,6 +162,36 @@ int tpc_profile_flush(tpc_ctx *ctx, const char **names, float *ms, int cap, int 
 /* Bytes of device memory the context currently holds. */
 int tpc_device_bytes(tpc_ctx *ctx, size_t *bytes);
 
+/* Largest batch tpc_cluster_static() accepts. */
+#define TPC_STATIC_MAX_HITS 65536
+
+/* One-shot clustering (variant TPC_LOCAL) of at most TPC_STATIC_MAX_HITS
+   hits that allocates nothing, for callers that cannot call cudaMalloc —
+   code running while a stream is captured into a CUDA graph, or real-time
+   readout loops that must not block on the allocator.  The paper has no
+   counterpart; it is an addition of this library.
+     hits        device pointer, n records (same layout as tpc_push)
+     labels      device pointer, n entries: labels[i] = smallest index i'
+                 in hit i's cluster (indices 0..n-1 of this call)
+     records     device pointer, record_cap cluster records ordered by label
+                 (as tpc_cluster_features); may be NULL if record_cap == 0
+     counts      device pointer, 2 entries written by the call:
+                 counts[0] = number of clusters, counts[1] = device error
+                 bits (0 = none; non-zero: a hit outside the sensor, a ToA
+                 span of 2^32 ticks or more, or more clusters than
+                 record_cap — records are then truncated)
+     stream      cudaStream_t (as void *) the work is queued on; 0 = legacy
+   Asynchronous: returns after queueing.  TPC_ERR_ARG for n >
+   TPC_STATIC_MAX_HITS, null pointers or a sensor larger than tpc_create
+   allows.  Working memory is one fixed device array of the library
+   (about 4.5 MB per GPU that loads it, held until exit), shared by every
+   call: calls whose work overlaps on the GPU race on it, so order them on
+   one stream.  The first call on a device looks up that array's address
+   and sets kernel attributes; make it before any stream capture. */
+int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width, uint32_t height,
+                       uint64_t dt, uint64_t *labels, tpc_cluster *records, size_t record_cap,
+                       uint64_t *counts, void *stream);
+
 const char *tpc_strerror(int status);
 void tpc_destroy(tpc_ctx *ctx);
 

@@ -43,6 +43,7 @@ SIGNATURES = {
     "tpc_device_bytes": ([_VP, ctypes.POINTER(_SZ)], _INT),
     "tpc_profile_flush": ([_VP, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                            _INT, ctypes.POINTER(_INT)], _INT),
+    "tpc_cluster_static": ([_VP, _SZ, _U32, _U32, _U64, _VP, _VP, _SZ, _VP, _VP], _INT),
     "tpc_strerror": ([_INT], ctypes.c_char_p),
     "tpc_destroy": ([_VP], None),
 }
