@@ -164,9 +164,13 @@ struct tpc_ctx {
     tpc_cluster *d_rec = nullptr;
     size_t out_cap = 0;
 
-    // where the last step's results live (own workspace or a batch's)
+    // where the last step's results live: the own workspace after a flush or
+    // push, the context's own result block after a batch (never another
+    // context's memory, which may be freed before this one is read)
     Seg *res_seg = nullptr;
     Prob *res_prob = nullptr;
+    Seg *own_res_seg = nullptr;
+    Prob *own_res_prob = nullptr;
     bool has_result = false;
     bool res_streaming = false;
     uint64_t res_base = 0;
@@ -473,6 +477,8 @@ int tpc_create(uint32_t width, uint32_t height, uint64_t dt, int variant, tpc_ct
         ok = cudaEventCreateWithFlags(&c->seg_ev[i], cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->own_res_seg, sizeof(Seg)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->own_res_prob, sizeof(Prob)) == cudaSuccess;
     if (!ok) { tpc_destroy(c); return TPC_ERR_CUDA; }
     *out = c;
     return TPC_OK;
@@ -709,6 +715,13 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
     }
     if (upload_segs(lead, lead->ws.w, segs.data(), n, lead->stream) != cudaSuccess) return TPC_ERR_CUDA;
     if (run_step(lead, lead->ws, n, lead->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {   // each context keeps its own copy of its results
+        if (cudaMemcpyAsync(ctxs[i]->own_res_seg, lead->ws.w.seg + i, sizeof(Seg), cudaMemcpyDeviceToDevice,
+                            lead->stream) != cudaSuccess ||
+            cudaMemcpyAsync(ctxs[i]->own_res_prob, lead->ws.w.prob, sizeof(Prob), cudaMemcpyDeviceToDevice,
+                            lead->stream) != cudaSuccess)
+            return TPC_ERR_CUDA;
+    }
     if (cudaEventRecord(lead->done_ev, lead->stream) != cudaSuccess) return TPC_ERR_CUDA;
     for (int i = 0; i < n; ++i) {
         tpc_ctx *c = ctxs[i];
@@ -717,8 +730,8 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
         c->pushed += c->pending;
         c->pending = 0;
         c->zc = nullptr;
-        c->res_seg = lead->ws.w.seg + i;
-        c->res_prob = lead->ws.w.prob;
+        c->res_seg = c->own_res_seg;
+        c->res_prob = c->own_res_prob;
         c->has_result = true;
         c->res_streaming = false;
     }
@@ -758,6 +771,8 @@ void tpc_destroy(tpc_ctx *c) {
     cudaFree(c->in);
     for (int i = 0; i < 2; ++i) { cudaFree(c->sbuf[i]); cudaFree(c->sgidx[i]); }
     cudaFree(c->ss);
+    cudaFree(c->own_res_seg);
+    cudaFree(c->own_res_prob);
     if (c->h_seg) cudaFreeHost(c->h_seg);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     for (int i = 0; i < SEG_RING; ++i) if (c->seg_ev[i]) cudaEventDestroy(c->seg_ev[i]);
