@@ -115,8 +115,11 @@ int tpc_set_option(tpc_ctx *ctx, int key, uint64_t value);
 int tpc_push(tpc_ctx *ctx, const tpc_hit *hits, size_t n, int where);
 
 /* Cluster everything pending and close every cluster (the end of the
-   stream).  Asynchronous: errors found on the device are reported by
-   tpc_sync() and the retrieval calls. */
+   stream).  Asynchronous for TPC_LOCAL: errors found on the device are
+   reported by tpc_sync() and the retrieval calls.  TPC_GLOBAL and
+   TPC_STATIC are clustered here too (TPC_GLOBAL waits for the device
+   between its merge rounds); streaming (max_disorder) and batching accept
+   TPC_LOCAL only. */
 int tpc_flush(tpc_ctx *ctx);
 
 /* Wait for the context's queued work; returns the first device-side error

@@ -420,14 +420,22 @@ cudaError_t init_kernel_attributes() {
     return e == cudaSuccess ? init_features_attributes() : e;
 }
 
-void launch_link(const Work &w, const Launch &L) {
+void launch_tile_border(const Work &w, const Launch &L) {
     const int smem = TILE_LINK_SMEM;
     k_tile_link<<<L.grid, LINK_THREADS, smem, L.stream>>>(w);
     L.mark("k_tile_link");
     k_border_link<<<L.grid, BORDER_THREADS, 0, L.stream>>>(w);
     L.mark("k_border_link");
+}
+
+void launch_flatten(const Work &w, const Launch &L) {
     k_flatten<<<L.grid, 256, 0, L.stream>>>(w);
     L.mark("k_flatten");
+}
+
+void launch_link(const Work &w, const Launch &L) {
+    launch_tile_border(w, L);
+    launch_flatten(w, L);
 }
 
 }  // namespace tpc

@@ -108,6 +108,37 @@ struct Workspace {
     }
 };
 
+// Arrays of the (b)/(c) variants, allocated on first use.
+struct VarSpace {
+    VarWork v{};
+    DevMem mem;
+    size_t pos_cap = 0, pixels = 0;
+    cudaError_t ensure(size_t positions, size_t npixels) {
+        if (v.k[0] && positions <= pos_cap && npixels <= pixels) return cudaSuccess;
+        cudaDeviceSynchronize();
+        mem.release();
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < 2; ++i) {
+            v.k[i] = mem.alloc<uint32_t>(positions, e);
+            v.v[i] = mem.alloc<uint32_t>(positions, e);
+        }
+        v.cpar = mem.alloc<uint32_t>(positions, e);
+        v.glast = mem.alloc<uint32_t>(positions, e);
+        v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
+        v.changed = mem.alloc<uint32_t>(1, e);
+        v.prob = mem.alloc<Prob>(1, e);
+        if (e != cudaSuccess) {
+            mem.release();
+            v = VarWork{};
+            pos_cap = pixels = 0;
+            return e;
+        }
+        pos_cap = positions;
+        pixels = npixels;
+        return cudaSuccess;
+    }
+};
+
 int num_sms(int dev) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
@@ -159,6 +190,8 @@ struct tpc_ctx {
     StreamState *ss = nullptr;
 
     Workspace ws;
+    VarSpace vs;                   // variants (b), (c)
+    uint32_t *h_flag = nullptr;    // pinned: (b) round result
     DevMem outmem;                 // output buffers
     uint64_t *d_labels = nullptr, *d_index = nullptr;
     tpc_cluster *d_rec = nullptr;
@@ -559,6 +592,69 @@ int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
     return TPC_OK;
 }
 
+// Variants (b) and (c): the (a) forest first, then the variant's kernels
+// (csrc/variants.cu), then the shared flatten / feature / output kernels.
+// Launched without a graph; (b) waits for the host between rounds.
+static int flush_variant(tpc_ctx *c, Tracer *tr) {
+    const size_t n = c->pending;
+    if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (c->vs.ensure(c->ws.pos_cap, (size_t)c->width * c->height) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (!c->h_flag && cudaMallocHost(&c->h_flag, sizeof(uint32_t)) != cudaSuccess) return TPC_ERR_NOMEM;
+    Seg s = base_seg(c);
+    s.hits = c->zc ? c->zc : c->in;
+    s.out_labels = c->d_labels;
+    s.out_rec = c->d_rec;
+    s.out_cap = (uint32_t)c->out_cap;
+    s.gidx_base = c->pushed;
+    s.n_new = (uint32_t)n;
+    if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    const Work &w = c->ws.w;
+    const VarWork &v = c->vs.v;
+    const Launch L{grid_of(c), c->stream, tr};
+    if (tr) cudaEventRecord(tr->ev[0], c->stream);
+    launch_setup(w, 1, L);
+    launch_prepare(w, L);
+    launch_seg_finalize(w, L);
+    launch_make_keys(w, L);
+    for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
+    launch_gather(w, L);
+    launch_tile_border(w, L);
+    launch_flatten(w, L);
+    const Work wv = variant_view(w, v);
+    if (c->variant == TPC_STATIC) {
+        launch_variant_keys(w, v, 0, L);
+        for (int pass = 0; pass < 4; ++pass) launch_radix_pass(wv, pass, L);
+        launch_static_sweep(w, v, L);
+    } else {
+        launch_variant_keys(w, v, 1, L);
+        for (int pass = 0; pass < 3; ++pass) launch_radix_pass(wv, pass, L);
+        launch_pixel_timelines(w, v, c->width * c->height, L);
+        for (int round = 0;; ++round) {
+            if (round > 4096) return TPC_ERR_TIMEOUT;
+            launch_global_round(w, v, L);
+            if (cudaMemcpyAsync(c->h_flag, v.changed, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return TPC_ERR_CUDA;
+            if (!*c->h_flag) break;
+        }
+    }
+    launch_flatten(w, L);
+    launch_features(w, L);
+    launch_outputs(w, L);
+    if (cudaGetLastError() != cudaSuccess) return TPC_ERR_CUDA;
+    c->res_base = c->pushed;
+    c->pushed += n;
+    c->pending = 0;
+    c->zc = nullptr;
+    c->res_seg = c->ws.w.seg;
+    c->res_prob = c->ws.w.prob;
+    c->has_result = true;
+    c->res_streaming = false;
+    return TPC_OK;
+}
+
 static int flush_impl(tpc_ctx *c, Tracer *tr) {
     if (c->max_disorder != ~0ull) {
         if (tr) return TPC_ERR_STATE;
@@ -566,7 +662,7 @@ static int flush_impl(tpc_ctx *c, Tracer *tr) {
         if (rc) return rc;
         return stream_step(c, 0, true);
     }
-    if (c->variant != TPC_LOCAL) return TPC_ERR_ARG;
+    if (c->variant != TPC_LOCAL) return flush_variant(c, tr);
     const size_t n = c->pending;
     if (over_budget(c, Workspace::bytes_for(n) > c->ws.mem.bytes ? Workspace::bytes_for(n) - c->ws.mem.bytes : 0))
         return TPC_ERR_BUSY;
@@ -773,6 +869,8 @@ void tpc_destroy(tpc_ctx *c) {
     cudaFree(c->ss);
     cudaFree(c->own_res_seg);
     cudaFree(c->own_res_prob);
+    c->vs.mem.release();
+    if (c->h_flag) cudaFreeHost(c->h_flag);
     if (c->h_seg) cudaFreeHost(c->h_seg);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     for (int i = 0; i < SEG_RING; ++i) if (c->seg_ev[i]) cudaEventDestroy(c->seg_ev[i]);

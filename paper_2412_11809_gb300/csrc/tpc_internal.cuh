@@ -118,6 +118,16 @@ struct Work {
     uint32_t *segtot;          // [MAX_SEGS][RADIX]
 };
 
+// Extra arrays of the (b)/(c) variants (single-segment steps only).
+struct VarWork {
+    uint32_t *k[2], *v[2];     // grouping radix sort: keys / sorted positions
+    uint32_t *cpar;            // (c): forest over the root-grouped order
+    uint32_t *glast;           // (b): per root, last key of its group
+    uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
+    uint32_t *changed;         // (b): a round merged something
+    Prob *prob;                // problem view of the grouping sort
+};
+
 // ---------------------------------------------------------------------------
 // device helpers
 
@@ -224,7 +234,14 @@ void launch_seg_finalize(const Work &w, const Launch &L);
 void launch_make_keys(const Work &w, const Launch &L);
 void launch_radix_pass(const Work &w, int pass, const Launch &L);
 void launch_gather(const Work &w, const Launch &L);
-void launch_link(const Work &w, const Launch &L);
+void launch_link(const Work &w, const Launch &L);          // tile + border + flatten
+void launch_tile_border(const Work &w, const Launch &L);
+void launch_flatten(const Work &w, const Launch &L);
+void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const Launch &L);
+Work variant_view(const Work &w, const VarWork &v);
+void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L);
+void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, const Launch &L);
+void launch_global_round(const Work &w, const VarWork &v, const Launch &L);
 void launch_features(const Work &w, const Launch &L);
 void launch_outputs(const Work &w, const Launch &L);
 

@@ -1,0 +1,241 @@
+// Variants (iii)(b) and (iii)(c) of the cluster definition (paper Section 2),
+// read as the time sweep of Algorithm 1: in (ToA, index) order a hit merges
+// every still-open cluster with a member on one of its 9 pixels; (b) open =
+// last ToA >= toa - dt, (c) open = first ToA >= toa - dt.  Both start from
+// the components of variant (a), already in the global forest.
+//
+// (c): every (c) join is an (a) edge (the joined member lies between the
+// cluster's first hit and the new hit, so within dt of it), hence (c)
+// clusters split (a) components and each component can be swept on its own.
+// Components are grouped by a stable radix sort on their root (keeping ToA
+// order inside); one thread sweeps each component, looking back only over
+// hits within dt (older members belong to clusters that are closed).
+//
+// (b): a closed cluster never reopens, so at any moment every open cluster
+// with a member on pixel p also contains the latest hit on p (that hit joined
+// it on arrival), and a (b) cluster is open exactly on [first, last + dt].
+// The sweep's result is therefore the least partition, reached from the (a)
+// components by merging, in which hit h is joined to L = the latest earlier
+// hit on each of its 9 pixels whenever toa(h) <= last(group(L)) + dt.
+// Rounds apply that rule with the groups' last ToA taken at the start of the
+// round (stale values only postpone merges) until a round merges nothing.
+// Per-pixel timelines come from a stable radix sort of the hits by pixel.
+#include "tpc_internal.cuh"
+
+namespace tpc {
+
+__device__ __forceinline__ bool adjacent_v(uint32_t a, uint32_t b) {
+    const int dx = (int)(a & 0xFFFFu) - (int)(b & 0xFFFFu);
+    const int dy = (int)(a >> 16) - (int)(b >> 16);
+    return dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
+}
+
+// grouping keys: (c) the (a) root of each sorted position; (b) its pixel id
+__global__ void __launch_bounds__(256) k_var_keys(Work w, VarWork v, int by_pixel) {
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const uint32_t *sroot = w.keys[sorted_sel(P) ^ 1u];
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
+            const uint32_t pix = w.spix[s];
+            v.k[0][s] = by_pixel ? (pix >> 16) * g.width + (pix & 0xFFFFu) : sroot[s];
+            v.v[0][s] = s;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *v.prob = P;
+        v.prob->npasses = by_pixel ? 3 : 4;   // pixel ids < 2^20; roots < 2^32
+    }
+}
+
+// find with path halving, for a forest owned by one thread
+__device__ __forceinline__ uint32_t seq_find(uint32_t *par, uint32_t x) {
+    while (par[x] != x) {
+        par[x] = par[par[x]];
+        x = par[x];
+    }
+    return x;
+}
+
+// (c): one thread per component start of the root-grouped order.
+__global__ void __launch_bounds__(128) k_static_sweep(Work w, VarWork v) {
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t sel = v.prob->npasses & 1u;
+    const uint32_t *gk = v.k[sel], *gv = v.v[sel];
+    uint32_t *cpar = v.cpar;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t last = g.off + g.n, dt = g.dt;
+        for (uint32_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
+            if (q != g.off && gk[q] == gk[q - 1]) continue;   // not the first of a component
+            uint32_t qe = q + 1;
+            while (qe < last && gk[qe] == gk[q]) ++qe;
+            for (uint32_t i = q; i < qe; ++i) cpar[i] = i;
+            for (uint32_t i = q + 1; i < qe; ++i) {
+                const uint32_t si = gv[i], ki = skey[si], pi = w.spix[si];
+                for (uint32_t j = i; j-- > q;) {
+                    const uint32_t sj = gv[j];
+                    if (ki - skey[sj] > dt) break;   // older members: clusters closed
+                    if (!adjacent_v(pi, w.spix[sj])) continue;
+                    const uint32_t rj = seq_find(cpar, j);
+                    if (ki - skey[gv[rj]] > dt) continue;   // cluster's first hit too old
+                    const uint32_t ri = seq_find(cpar, i);
+                    if (ri != rj) {   // the earlier root stays root (first ToA)
+                        if (ri < rj) cpar[rj] = ri; else cpar[ri] = rj;
+                    }
+                }
+            }
+            for (uint32_t i = q; i < qe; ++i) w.parent[gv[i]] = gv[seq_find(cpar, i)];
+        }
+    }
+}
+
+// (b): pixel histogram and its exclusive scan (single segment).
+__global__ void __launch_bounds__(256) k_pixel_hist(Work w, VarWork v) {
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
+            const uint32_t pix = w.spix[s];
+            atomicAdd(&v.pix_start[(pix >> 16) * g.width + (pix & 0xFFFFu) + 1], 1u);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_pixel_scan(Work w, VarWork v) {
+    __shared__ uint32_t s_warp[32];
+    const Seg &g = w.seg[0];
+    const uint32_t np = g.width * g.height;   // entries 1..np hold counts
+    const uint32_t per = (np + blockDim.x - 1) / blockDim.x;
+    const uint32_t i0 = 1 + threadIdx.x * per;
+    uint32_t local = 0;
+    for (uint32_t i = i0; i < i0 + per && i <= np; ++i) local += v.pix_start[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t run = x - local;
+    for (int q = 0; q < warp; ++q) run += s_warp[q];
+    for (uint32_t i = i0; i < i0 + per && i <= np; ++i) {
+        run += v.pix_start[i];
+        v.pix_start[i] = run;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_group_last_reset(Work w, VarWork v) {
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x)
+            if (w.parent[s] == s) v.glast[s] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_group_last(Work w, VarWork v) {
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const uint32_t *skey = w.keys[sorted_sel(P)];
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x)
+            atomicMax(&v.glast[gfind(w.parent, s)], skey[s]);
+    }
+}
+
+// (b): one round of merges along (h, latest earlier hit on each 9-pixel).
+__global__ void __launch_bounds__(256) k_global_round(Work w, VarWork v) {
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *tl = v.v[v.prob->npasses & 1u];   // sorted positions grouped by pixel
+    bool changed = false;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t W = g.width, H = g.height, dt = g.dt;
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
+            const uint32_t key = skey[s], pix = w.spix[s];
+            const int x = (int)(pix & 0xFFFFu), y = (int)(pix >> 16);
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int ny = y + dy;
+                if (ny < 0 || ny >= (int)H) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int nx = x + dx;
+                    if (nx < 0 || nx >= (int)W) continue;
+                    const uint32_t p = (uint32_t)ny * W + (uint32_t)nx;
+                    uint32_t lo = v.pix_start[p], hi = v.pix_start[p + 1];   // last entry < s
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (tl[g.off + mid] < s) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo == v.pix_start[p]) continue;
+                    const uint32_t L = tl[g.off + lo - 1];
+                    const uint32_t rl = gfind(w.parent, L), rh = gfind(w.parent, s);
+                    if (rl == rh) continue;
+                    if ((uint64_t)key <= (uint64_t)v.glast[rl] + dt) {
+                        gunion(w.parent, s, L);
+                        changed = true;
+                    }
+                }
+            }
+        }
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(v.changed, 1u);
+}
+
+void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const Launch &L) {
+    k_var_keys<<<L.grid, 256, 0, L.stream>>>(w, v, by_pixel);
+    L.mark(by_pixel ? "k_var_keys_pixel" : "k_var_keys_root");
+}
+
+Work variant_view(const Work &w, const VarWork &v) {
+    Work wv = w;
+    wv.keys[0] = v.k[0];
+    wv.keys[1] = v.k[1];
+    wv.vals[0] = v.v[0];
+    wv.vals[1] = v.v[1];
+    wv.prob = v.prob;
+    return wv;
+}
+
+void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L) {
+    k_static_sweep<<<L.grid, 128, 0, L.stream>>>(w, v);
+    L.mark("k_static_sweep");
+}
+
+void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, const Launch &L) {
+    cudaMemsetAsync(v.pix_start, 0, (npixels + 1) * sizeof(uint32_t), L.stream);
+    k_pixel_hist<<<L.grid, 256, 0, L.stream>>>(w, v);
+    k_pixel_scan<<<1, 1024, 0, L.stream>>>(w, v);
+    L.mark("k_pixel_hist_scan");
+}
+
+void launch_global_round(const Work &w, const VarWork &v, const Launch &L) {
+    cudaMemsetAsync(v.changed, 0, sizeof(uint32_t), L.stream);
+    k_group_last_reset<<<L.grid, 256, 0, L.stream>>>(w, v);
+    k_group_last<<<L.grid, 256, 0, L.stream>>>(w, v);
+    k_global_round<<<L.grid, 256, 0, L.stream>>>(w, v);
+    L.mark("k_global_round");
+}
+
+}  // namespace tpc

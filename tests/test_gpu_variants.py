@@ -1,0 +1,76 @@
+"""Variants (iii)(b) and (iii)(c) of the cluster definition (paper Section 2)
+on the device, against the oracle's time sweep (Algorithm 1 reading):
+labels bit-exact, integer features exact, centroids within 1e-5 relative.
+Also every hand-derived golden fixture through the CUDA path."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from bruteforce import random_hits
+from golden_cases import all_cases
+from gpu_helpers import check_against_oracle, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.mark.parametrize("case", all_cases(), ids=lambda c: c["name"])
+def test_golden_all_variants(case):
+    for v, want in case["expect"].items():
+        lab, _ = run_gpu(case["hits"], case["width"], case["height"], case["dt"], v)
+        np.testing.assert_array_equal(lab, want, err_msg=f"{case['name']} {v}")
+
+
+@pytest.mark.parametrize("variant", ["global", "static"])
+def test_cfg0_scaled(variant):
+    hits, _ = synth.cfg0(scale=0.25, seed=21)
+    check_against_oracle(hits, 256, 256, 128, variant)
+
+
+@pytest.mark.parametrize("variant", ["global", "static"])
+@pytest.mark.parametrize("dt", [128, 384])
+def test_cfg1_scaled(variant, dt):
+    hits, _ = synth.cfg1(scale=1 / 64, seed=22)
+    check_against_oracle(hits, 256, 256, dt, variant)
+
+
+@pytest.mark.parametrize("variant", ["global", "static"])
+def test_cfg4_timepix4_scaled(variant):
+    hits, _ = synth.cfg4(scale=1 / 512, seed=23)
+    check_against_oracle(hits, 448, 512, 128, variant)
+
+
+@pytest.mark.parametrize("variant", ["global", "static"])
+@pytest.mark.parametrize("seed", range(6))
+def test_random_dense(variant, seed):
+    rng = np.random.default_rng(300 + seed)
+    w, h = int(rng.integers(1, 12)), int(rng.integers(1, 12))
+    n = int(rng.integers(2000, 12000))
+    hits = random_hits(rng, n, w, h, int(rng.integers(0, 3 * n)))
+    check_against_oracle(hits, w, h, int(rng.integers(0, 40)), variant)
+
+
+@pytest.mark.parametrize("variant", ["global", "static"])
+def test_edge_cases(variant):
+    one = oracle.make_hits([3], [2], [5])
+    check_against_oracle(one, 4, 3, 0, variant)
+    pile = oracle.make_hits(np.zeros(5000, int), np.zeros(5000, int), np.arange(5000)[::-1] * 2)
+    check_against_oracle(pile, 1, 1, 3, variant)
+    check_against_oracle(pile, 1, 1, 1, variant)
+    rng = np.random.default_rng(9)
+    same = random_hits(rng, 8000, 60, 40, 0)
+    check_against_oracle(same, 60, 40, 0, variant)
+
+
+def test_refinement_on_device():
+    hits, _ = synth.cfg1(scale=1 / 128, seed=24)
+    a, _ = run_gpu(hits, 256, 256, 128, "local")
+    b, _ = run_gpu(hits, 256, 256, 128, "global")
+    c, _ = run_gpu(hits, 256, 256, 128, "static")
+    ai, bi, ci = (x.astype(np.int64) for x in (a, b, c))
+    assert np.all(a == a[ci])      # (c) refines (a)
+    assert np.all(b == b[ai])      # (a) refines (b)
