@@ -39,6 +39,8 @@ PAPER_CONTEXT = ("paper: up to 300 Mhits/s end-to-end (H2D+D2H) on RTX 4070 Ti S
                  "RTX 3060 Laptop over PCIe 4.0, dataset unstated")
 DT = 128
 W = H = 256
+HIT_DTYPE_NP = np.dtype([("x", "<u2"), ("y", "<u2"), ("tot", "<u2"), ("reserved", "<u2"),
+                         ("toa", "<u8")])
 
 # Algorithmic bytes per hit of each kernel: the unique data it must move
 # (records 16 B, keys/positions/pixels/parents 4 B, labels 8 B); the cluster
@@ -57,6 +59,30 @@ def path_bytes_per_hit(n_hits: int, n_clusters: int) -> float:
     """B_alg of the whole path: read the 16-byte record, write the 8-byte
     label, write a 40-byte record per cluster."""
     return 16 + 8 + 40 * n_clusters / max(n_hits, 1)
+
+
+def kernel_source_sha() -> str:
+    """Hash of the CUDA sources: a stored ncu traffic figure is only valid for the
+    build it was captured on."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2412_11809_gb300", "csrc", "*.cu*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel: str, n_hits: int):
+    """DRAM bytes per launch of `kernel` at n_hits, from profiles/traffic.json
+    (written from an ncu capture of the same sources), else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha") != kernel_source_sha():
+        return None
+    return rec["dram_bytes_per_hit"] * n_hits
 
 
 def measured_peak_gbs() -> tuple[float, str]:
@@ -171,6 +197,126 @@ def run_reference(args):
     return 0
 
 
+def run_serving(args, dev, torch):
+    """8 streams, chunks log-uniform in [64k, 2M] hits, each stream's base
+    stream replayed with a ToA offset (as the paper repeats its data, Section 4)
+    until enough chunks; one host thread and one CUDA stream per detector.
+    Latency per chunk: push (H2D from pinned memory) to labels and records of
+    the finalised clusters back on the host."""
+    import threading
+    import synth
+    from paper_2412_11809_gb300 import CLUSTER_DTYPE, Clusterer
+    streams = synth.cfg3(hits_per_stream=args.serving_hits, n_streams=8, seed=3000)
+    reps = max(1, -(-args.serving_chunks // sum(len(s[1]) for s in streams)))
+    lat, straddle = [[] for _ in streams], []
+    totals = [0] * len(streams)
+    errors = []
+
+    def worker(i):
+        try:
+            hits, sizes, t = streams[i]
+            span = int(hits["toa"].max() - hits["toa"].min()) + 10 * 128
+            ctx = Clusterer(W, H, DT, max_disorder=t, stream=torch.cuda.Stream(device=dev))
+            cap = 2 * max(sizes) + 1_000_000
+            pin_lab = torch.empty(cap, dtype=torch.int64).pin_memory()
+            pin_idx = torch.empty(cap, dtype=torch.int64).pin_memory()
+            pin_rec = torch.empty((cap, CLUSTER_DTYPE.itemsize), dtype=torch.uint8).pin_memory()
+            chunks = []
+            start = 0
+            for s in sizes:
+                chunks.append(torch.from_numpy(hits[start:start + s].view(np.uint8).reshape(-1, 16)).pin_memory())
+                start += s
+            first_lab, first_idx = [], []
+            for r in range(reps):
+                for k, ch in enumerate(chunks):
+                    if r:   # replay with a ToA offset: a later, t-ordered continuation
+                        view = ch.numpy().view(HIT_DTYPE_NP).reshape(-1)
+                        view["toa"] += np.uint64(span)
+                    t0 = time.perf_counter()
+                    ctx.push_ptr(ch.data_ptr(), ch.shape[0], device=False)
+                    m = ctx.labels_into(pin_lab.data_ptr(), cap, device=False, indices_ptr=pin_idx.data_ptr())
+                    ctx.features_into(pin_rec.data_ptr(), cap, device=False)
+                    lat[i].append(time.perf_counter() - t0)
+                    totals[i] += ch.shape[0]
+                    if r == 0:
+                        first_lab.append(pin_lab[:m].numpy().copy())
+                        first_idx.append(pin_idx[:m].numpy().copy())
+            ctx.flush()
+            ctx.sync()
+            ctx.close()
+            if first_lab:
+                lab = np.concatenate(first_lab)
+                idx = np.concatenate(first_idx)
+                chunk_of = np.searchsorted(np.cumsum(sizes), idx, side="right")
+                lab_chunk = np.searchsorted(np.cumsum(sizes), lab, side="right")
+                crossing = np.unique(lab[chunk_of != lab_chunk])
+                straddle.append(len(crossing) / max(1, len(np.unique(lab))))
+        except Exception as e:   # reported in the JSON line
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(streams))]
+    t0 = time.perf_counter()
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    wall = time.perf_counter() - t0
+    all_lat = np.array([v for l in lat for v in l]) * 1e3
+    out = {"streams": len(streams), "chunks": int(len(all_lat)), "chunk_hits": "log-uniform 64k-2M",
+           "hits_per_s": sum(totals) / wall if wall > 0 else None,
+           "p50_ms": float(np.percentile(all_lat, 50)) if len(all_lat) else None,
+           "p99_ms": float(np.percentile(all_lat, 99)) if len(all_lat) else None,
+           "straddling_cluster_frac": float(np.mean(straddle)) if straddle else None,
+           "latency": "host push (pinned H2D) to finalised labels+records on host, per chunk"}
+    if errors:
+        out["errors"] = errors[:3]
+    return out
+
+
+def run_batched(args, dev, torch):
+    """16 detectors (ten 256x256, six 448x512): one batched step (one CUDA-graph
+    replay, persistent CTAs over every detector's tiles) against one flush per
+    detector, inputs resident on the device."""
+    import synth
+    from paper_2412_11809_gb300 import Clusterer, batch_flush
+    dets = synth.cfg2(scale=args.batch_scale, seed=2000)
+    dev_hits = [torch.from_numpy(h.view(np.uint8).reshape(-1, 16)).to(dev) for _, _, h, _, _ in dets]
+    n_total = sum(len(h) for _, _, h, _, _ in dets)
+    stream = torch.cuda.Stream(device=dev)
+    ctxs = [Clusterer(w, h, DT, stream=stream) for w, h, _, _, _ in dets]
+
+    def batched():
+        for c, d in zip(ctxs, dev_hits):
+            c.push(d)
+        batch_flush(ctxs)
+        for c in ctxs:
+            c.sync()
+
+    def single():
+        for c, d in zip(ctxs, dev_hits):
+            c.push(d)
+            c.flush()
+        for c in ctxs:
+            c.sync()
+
+    res = {}
+    for name, fn in (("batched", batched), ("one_launch_per_detector", single)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        res[name] = n_total * 3 / (e0.elapsed_time(e1) / 1e3)
+    for c in ctxs:
+        c.close()
+    return {"detectors": len(dets), "hits": n_total, "hits_per_s": res["batched"],
+            "one_launch_per_detector_hits_per_s": res["one_launch_per_detector"]}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -273,6 +419,11 @@ def run_gpu(args):
                "sample": f"first {n_sample} hits of the same stream, labels + features, "
                          f"single-threaded on a host with {cpu_cores()} cores"}
 
+    serving = batched = None
+    if rank == 0 and not args.no_extras:
+        batched = run_batched(args, dev, torch)
+        serving = run_serving(args, dev, torch)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "hits/s", "n_gpus": world,
@@ -284,7 +435,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}", "paper_context": PAPER_CONTEXT},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": stored_traffic(dominant, n),
                          "bytes_per_hit": KERNEL_BYTES_PER_HIT.get(dominant, 0),
                          "kernel_ms": prof_ms[dominant]},
             "path_roofline": {"bytes_per_hit": b_alg, "achieved": path_gbs, "peak": peak,
@@ -295,6 +446,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": 8 * n + CLUSTER_DTYPE.itemsize * m},
             "gpu_launches": n_kernels * args.steps,
             "clocks": clocks.summary(),
+            "serving": serving,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     c.close()
@@ -313,6 +466,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16 * 2**20)
     ap.add_argument("--ref-sample", type=int, default=4 * 2**20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the serving and batched lines")
+    ap.add_argument("--serving-hits", type=int, default=4 * 2**20, help="base hits per serving stream")
+    ap.add_argument("--serving-chunks", type=int, default=1024)
+    ap.add_argument("--batch-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
