@@ -47,10 +47,19 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
         for (uint32_t b = begin; b < end; b += ACC_SPAN) {
             const uint32_t e = b + ACC_SPAN < end ? b + ACC_SPAN : end;
             uint32_t rr[ACC_ITEMS];
+            uint32_t px[ACC_ITEMS], tt[ACC_ITEMS], kk[ACC_ITEMS], ps[ACC_ITEMS];
 #pragma unroll
-            for (int q = 0; q < ACC_ITEMS; ++q) {
+            for (int q = 0; q < ACC_ITEMS; ++q) {   // every load in flight before any use
                 const uint32_t s = b + q * ACC_THREADS + threadIdx.x;
-                rr[q] = s < e ? sroot[s] : 0;
+                if (s < e) {
+                    rr[q] = sroot[s];
+                    px[q] = w.spix[s];
+                    tt[q] = w.stot[s];
+                    kk[q] = skey[s];
+                    ps[q] = sidx[s];
+                } else {
+                    rr[q] = 0;
+                }
             }
 #pragma unroll
             for (int q = 0; q < ACC_ITEMS; ++q) {
@@ -67,7 +76,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
                 const uint32_t s = b + q * ACC_THREADS + threadIdx.x;
                 if (s >= e) continue;
                 const uint32_t r = rr[q];
-                const uint32_t pix = w.spix[s], tot = w.stot[s], key = skey[s], pos = sidx[s];
+                const uint32_t pix = px[q], tot = tt[q], key = kk[q], pos = ps[q];
                 const uint32_t wx = tot * (pix & 0xFFFFu), wy = tot * (pix >> 16);
                 if (r >= b) {
                     const uint32_t k = r - b;

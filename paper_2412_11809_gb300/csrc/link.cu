@@ -33,6 +33,7 @@
 namespace tpc {
 
 constexpr int LINK_THREADS = 512;
+constexpr uint32_t TAB_PIXELS = 1u << 16;      // table mode up to this many pixels
 constexpr int NBUCKETS = 2048;                // hashed 4x4-pixel cells
 constexpr int HALO_BATCH = 2048;
 constexpr int BORDER_THREADS = 256;
@@ -238,18 +239,30 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
     static_assert(2 * NBUCKETS + 1 >= TILE + 1, "prefix array size");
 
     const Prob &P = *w.prob;
-    const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    // tiles of large sensors, then the tiles the table kernel gave back
+    const uint32_t n_large = P.ntiles, n_all = P.ntiles + P.redo_count;
+    for (uint32_t u = blockIdx.x; u < n_all; u += gridDim.x) {
+        const uint32_t t = u < n_large ? u : w.redo[u - n_large];
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         const uint32_t n_t = end - begin, W = g.width, H = g.height, dt = g.dt;
+        if (u < n_large && W * H <= TAB_PIXELS) continue;   // done by k_tile_link_table
         const uint32_t cw = (W + 3) >> 2;
-        for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS) {
-            s_key[k] = skey[begin + k];
-            s_pix[k] = w.spix[begin + k];
-            s_par[k] = k;
+        {
+            constexpr int ITEMS = TILE / LINK_THREADS;
+            uint32_t kv[ITEMS], pv[ITEMS];
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {   // every load in flight before any use
+                const uint32_t k = q * LINK_THREADS + threadIdx.x;
+                if (k < n_t) { kv[q] = skey[begin + k]; pv[q] = w.spix[begin + k]; }
+            }
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t k = q * LINK_THREADS + threadIdx.x;
+                if (k < n_t) { s_key[k] = kv[q]; s_pix[k] = pv[q]; s_par[k] = k; }
+            }
         }
         __syncthreads();
         // mean window length (hits within dt before a hit) decides the mode
@@ -289,6 +302,182 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
         __syncthreads();
         for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS)
             w.parent[begin + k] = begin + s_min[s_root[k]];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Table mode, for sensors of at most TAB_PIXELS pixels: a direct-mapped
+// per-pixel table in shared memory (the paper's per-pixel matrix with 2-byte
+// entries, Algorithm 3 step 4 and Section 4.2) heads a lock-free list of the
+// tile's hits on each pixel (16-bit compare-and-swap pushes).  Hit k walks the
+// lists of its 9 pixels; every earlier hit there within dt is an edge.
+//
+// Components without contended union-find: each hit points to the first
+// earlier neighbour it found (a forest, since parents have smaller ranks);
+// further neighbours go to an edge list.  Pointer jumping flattens the
+// forest, then each listed edge whose ends have different roots hooks the
+// larger root under the smaller (atomicMin); flatten and hook repeat until no
+// edge hooks (Shiloach-Vishkin style).  The surviving root of a component is
+// its smallest rank, i.e. its earliest hit.  A list longer than TAB_WALK (a
+// pile on one pixel) or more edges than the list holds send the tile to
+// k_tile_link instead.  Only the table entries a tile touched are reset
+// afterwards (Algorithm 3 step 7).
+constexpr int TAB_THREADS = 1024;
+constexpr uint16_t TAB_NONE = 0xFFFFu;
+constexpr int TAB_WALK = 64;
+constexpr int TAB_EDGES = 2 * TILE;
+
+struct TabShared {
+    uint16_t tab[TAB_PIXELS];        // head of each pixel's list (rank), or TAB_NONE
+    uint32_t key[TILE];
+    uint32_t pix[TILE];
+    uint32_t par[TILE];              // forest over ranks
+    uint16_t next[TILE];             // next rank on the same pixel
+    uint32_t edges[TAB_EDGES];       // extra edges, k << 16 | j
+    uint32_t nedges;
+    uint32_t overflow;
+};
+constexpr int TAB_SMEM = (int)sizeof(TabShared);
+
+__device__ __forceinline__ uint32_t tab_pid(uint32_t pix, uint32_t W) {
+    return (pix >> 16) * W + (pix & 0xFFFFu);
+}
+
+// push rank k on pixel pid's list; returns the previous head
+__device__ __forceinline__ uint16_t tab_push(uint16_t *tab, uint32_t pid, uint16_t k) {
+    uint32_t *word = reinterpret_cast<uint32_t *>(tab) + (pid >> 1);
+    const uint32_t shift = (pid & 1u) * 16u;
+    uint32_t old = *reinterpret_cast<volatile uint32_t *>(word);
+    while (true) {
+        const uint32_t nv = (old & ~(0xFFFFu << shift)) | ((uint32_t)k << shift);
+        const uint32_t seen = atomicCAS(word, old, nv);
+        if (seen == old) return (uint16_t)(old >> shift);
+        old = seen;
+    }
+}
+
+// root of k by pointer jumping (parents only ever move towards the root)
+__device__ __forceinline__ uint32_t tab_root(volatile uint32_t *par, uint32_t k) {
+    uint32_t p = par[k];
+    while (true) {
+        const uint32_t q = par[p];
+        if (q == p) return p;
+        par[k] = q;
+        p = q;
+    }
+}
+
+__global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
+    extern __shared__ __align__(16) unsigned char tab_raw[];
+    TabShared &S = *reinterpret_cast<TabShared *>(tab_raw);
+    volatile uint32_t *vpar = S.par;
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t i = threadIdx.x; i < TAB_PIXELS / 2; i += TAB_THREADS)
+        reinterpret_cast<uint32_t *>(S.tab)[i] = 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        const uint32_t W = g.width, H = g.height, dt = g.dt;
+        if (W * H > TAB_PIXELS) continue;   // k_tile_link handles larger sensors
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t n_t = end - begin;
+        constexpr int ITEMS = TILE / TAB_THREADS;   // 4
+        uint32_t kv[ITEMS], pv[ITEMS];
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t k = q * TAB_THREADS + threadIdx.x;
+            if (k < n_t) { kv[q] = skey[begin + k]; pv[q] = w.spix[begin + k]; }
+        }
+        if (threadIdx.x == 0) { S.overflow = 0; S.nedges = 0; }
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t k = q * TAB_THREADS + threadIdx.x;
+            if (k < n_t) {
+                S.key[k] = kv[q];
+                S.pix[k] = pv[q];
+                S.next[k] = tab_push(S.tab, tab_pid(pv[q], W), (uint16_t)k);
+            }
+        }
+        __syncthreads();
+        // neighbour walk: first earlier neighbour = parent, the rest = edges
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t k = q * TAB_THREADS + threadIdx.x;
+            uint32_t parent = k;
+            if (k < n_t) {
+                const uint32_t key = kv[q];
+                const int x = (int)(pv[q] & 0xFFFFu), y = (int)(pv[q] >> 16);
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int ny = y + dy;
+                    if (ny < 0 || ny >= (int)H) continue;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int nx = x + dx;
+                        if (nx < 0 || nx >= (int)W) continue;
+                        uint32_t j = S.tab[(uint32_t)ny * W + (uint32_t)nx];
+                        int steps = 0;
+                        for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps) {
+                            if (j >= k || key - S.key[j] > dt) continue;
+                            if (parent == k) {
+                                parent = j;
+                            } else {
+                                const uint32_t slot = atomicAdd(&S.nedges, 1u);
+                                if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | j;
+                            }
+                        }
+                        if (j != TAB_NONE) S.overflow = 1;
+                    }
+                }
+                S.par[k] = parent;
+            }
+        }
+        __syncthreads();
+        if (S.overflow || S.nedges > TAB_EDGES) {   // leave this tile to k_tile_link
+            if (threadIdx.x == 0) {
+                const uint32_t slot = atomicAdd(&w.prob->redo_count, 1u);
+                w.redo[slot] = t;
+            }
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                if (k < n_t) S.tab[tab_pid(pv[q], W)] = TAB_NONE;
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint32_t ne = S.nedges;
+        while (true) {
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {   // flatten
+                const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                if (k < n_t) vpar[k] = tab_root(vpar, k);
+            }
+            __syncthreads();
+            bool hooked = false;
+            for (uint32_t e = threadIdx.x; e < ne; e += TAB_THREADS) {   // hook
+                const uint32_t ed = S.edges[e];
+                const uint32_t ra = vpar[ed >> 16], rb = vpar[ed & 0xFFFFu];
+                if (ra != rb) {
+                    atomicMin(&S.par[ra > rb ? ra : rb], ra < rb ? ra : rb);
+                    hooked = true;
+                }
+            }
+            if (!__syncthreads_or(hooked)) break;
+        }
+        (void)lt;
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            const uint32_t k = q * TAB_THREADS + threadIdx.x;
+            if (k < n_t) {
+                w.parent[begin + k] = begin + vpar[k];
+                S.tab[tab_pid(pv[q], W)] = TAB_NONE;   // reset only what this tile touched
+            }
+        }
         __syncthreads();
     }
 }
@@ -417,11 +606,16 @@ cudaError_t init_features_attributes();
 
 cudaError_t init_kernel_attributes() {
     cudaError_t e = cudaFuncSetAttribute(k_tile_link, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_LINK_SMEM);
-    return e == cudaSuccess ? init_features_attributes() : e;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tile_link_table, cudaFuncAttributeMaxDynamicSharedMemorySize, TAB_SMEM);
+    if (e == cudaSuccess) e = init_features_attributes();
+    return e == cudaSuccess ? init_sortfast_attributes() : e;
 }
 
 void launch_tile_border(const Work &w, const Launch &L) {
     const int smem = TILE_LINK_SMEM;
+    k_tile_link_table<<<L.sms > 0 ? L.sms : L.grid, TAB_THREADS, TAB_SMEM, L.stream>>>(w);
+    L.mark("k_tile_link_table");
     k_tile_link<<<L.grid, LINK_THREADS, smem, L.stream>>>(w);
     L.mark("k_tile_link");
     k_border_link<<<L.grid, BORDER_THREADS, 0, L.stream>>>(w);

@@ -32,7 +32,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // byte offsets of every work array inside the scratch array
 struct Layout {
-    size_t seg, prob, tile_seg, keys0, keys1, vals0, vals1, spix, stot, parent, root_of,
+    size_t seg, prob, tile_seg, redo, keys0, keys1, vals0, vals1, spix, stot, parent, root_of,
         slot_size, slot_min, slot_maxkey, slot_tot, slot_wx, slot_wy, flag_label, flag_closed,
         tile_cnt, tile_base, hist, segtot, total;
 };
@@ -43,6 +43,7 @@ constexpr Layout make_layout() {
     l.seg = o; o += align256(sizeof(Seg));
     l.prob = o; o += align256(sizeof(Prob));
     l.tile_seg = o; o += align256(NA_TILES * 4);
+    l.redo = o; o += align256(NA_TILES * 4);
     l.keys0 = o; o += align256(NA_POS * 4);
     l.keys1 = o; o += align256(NA_POS * 4);
     l.vals0 = o; o += align256(NA_POS * 4);
@@ -143,6 +144,7 @@ extern "C" int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width,
     w.seg = reinterpret_cast<Seg *>(base + NA.seg);
     w.prob = reinterpret_cast<Prob *>(base + NA.prob);
     w.tile_seg = reinterpret_cast<uint32_t *>(base + NA.tile_seg);
+    w.redo = reinterpret_cast<uint32_t *>(base + NA.redo);
     w.keys[0] = reinterpret_cast<uint32_t *>(base + NA.keys0);
     w.keys[1] = reinterpret_cast<uint32_t *>(base + NA.keys1);
     w.vals[0] = reinterpret_cast<uint32_t *>(base + NA.vals0);
@@ -178,11 +180,12 @@ extern "C" int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width,
     s.dt = dt > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)dt;
     s.variant = TPC_LOCAL;
 
-    const Launch L{sms * 4, st};
+    const Launch L{sms * 4, st, nullptr, sms};
     k_na_begin<<<1, 1, 0, st>>>(w, s, NA_TILES, NA_POS);
     launch_setup(w, 1, L);
     launch_prepare(w, L);
     launch_seg_finalize(w, L);
+    launch_sort_fast(w, L);
     launch_make_keys(w, L);
     for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
     launch_gather(w, L);

@@ -43,6 +43,9 @@ __global__ void k_setup(Work w, int nsegs) {
         Prob &p = *w.prob;
         p.nsegs = (uint32_t)nsegs;
         p.npasses = 0;
+        p.fallback = 0;
+        p.lsd_passes = 0;
+        p.redo_count = 0;
         p.err = 0;
         p.ntiles = tile;
         if (tile > p.tile_cap || off > p.pos_cap) {
@@ -153,7 +156,7 @@ __global__ void k_seg_finalize(Work w) {
             }
         }
         g.npasses = passes;
-        atomicMax(&w.prob->npasses, passes);
+        atomicMax(&w.prob->lsd_passes, passes);   // used only if the fast sort falls back
         if (!g.ss) {
             g.close_mode = CLOSE_ALL;   // one-shot: the end of the stream
             continue;
@@ -178,8 +181,9 @@ __global__ void k_seg_finalize(Work w) {
     }
 }
 
-// keys[pos] = ToA - toa_min (32 bits), vals[pos] = pos.
+// Fallback path: keys[pos] = ToA - toa_min (32 bits), vals[pos] = pos.
 __global__ void __launch_bounds__(256) k_make_keys(Work w) {
+    if (!w.prob->fallback) return;
     const uint32_t nt = w.prob->ntiles;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
@@ -206,8 +210,9 @@ __global__ void __launch_bounds__(256) k_make_keys(Work w) {
     }
 }
 
-// spix[s], stot[s] = pixel and ToT of the hit at sorted position s.
+// Fallback path: spix[s], stot[s] = pixel and ToT of the hit at sorted position s.
 __global__ void __launch_bounds__(256) k_gather(Work w) {
+    if (!w.prob->fallback) return;   // the tile sort wrote pixels and ToTs already
     const uint32_t nt = w.prob->ntiles;
     const uint32_t *vals = w.vals[sorted_sel(*w.prob)];
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {

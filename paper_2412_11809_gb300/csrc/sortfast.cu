@@ -1,0 +1,307 @@
+// ToA ordering for t-ordered streams (Section 3.1: each hit arrives at most
+// t late), in three kernels, with the general LSD radix sort (radix.cu) as
+// the fallback:
+//
+//   k_tile_sort   every tile of TILE input positions is loaded once (16-byte
+//                 vector loads) and sorted in shared memory by a block radix
+//                 sort over the key bits that vary inside the tile; the
+//                 sorted keys, positions, pixels and ToTs are written out, so
+//                 no separate gather is needed.
+//   k_tile_merge  the second half of tile t-1 and the first half of tile t
+//                 are merged (merge path).  If every hit lies less than TILE/2
+//                 positions from its place in (ToA, position) order, this
+//                 completes the sort: after the first kernel, the prefix
+//                 ending in the middle of any tile holds exactly the hits that
+//                 belong there, so the windows straddling tile borders only
+//                 need their own contents ordered.
+//   k_sort_check  compares the neighbours at every window border; on any
+//                 inversion the problem is marked for the fallback, whose
+//                 kernels (make_keys, radix passes, gather) otherwise return
+//                 at once.  The result is therefore exact for any input
+//                 order.
+#include "tpc_internal.cuh"
+
+namespace tpc {
+
+constexpr int LS_THREADS = 256;
+constexpr int LS_WARPS = LS_THREADS / 32;
+constexpr int LS_ITEMS = TILE / LS_THREADS;    // 16
+constexpr int LS_WARP_SPAN = TILE / LS_WARPS;  // 512
+constexpr uint16_t LS_NONE = 0xFFFFu;
+
+__device__ __forceinline__ uint32_t ls_lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t ls_match_digit(uint32_t d, uint32_t vmask) {
+    uint32_t peers = vmask;
+#pragma unroll
+    for (int b = 0; b < RADIX_BITS; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
+struct LsShared {
+    uint32_t key[TILE];
+    uint32_t pix[TILE];
+    uint16_t tot[TILE];
+    uint16_t idx[TILE];          // local input index of the element at each rank
+    uint32_t wcnt[LS_WARPS][RADIX];
+    uint32_t dstart[RADIX];
+    uint32_t warp[32];
+    uint32_t kmin[LS_WARPS], kmax[LS_WARPS];
+};
+
+constexpr int LS_SMEM = (int)sizeof(LsShared);
+
+__global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
+    extern __shared__ __align__(16) unsigned char ls_raw[];
+    LsShared &S = *reinterpret_cast<LsShared *>(ls_raw);
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = ls_lanemask_lt();
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t n_t = end - begin;
+        const tpc_hit *hits = g.hits + (begin - g.off);
+        const uint64_t base = g.toa_min;
+        uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
+        constexpr int HALF = LS_ITEMS / 2;   // two batches of loads keep registers in bounds
+#pragma unroll
+        for (int hb = 0; hb < 2; ++hb) {
+            uint4 hv[HALF];
+#pragma unroll
+            for (int r = 0; r < HALF; ++r) {
+                const uint32_t li = (hb * HALF + r) * LS_THREADS + threadIdx.x;
+                if (li < n_t) hv[r] = ld_hit(hits + li);
+            }
+#pragma unroll
+            for (int r = 0; r < HALF; ++r) {
+                const uint32_t li = (hb * HALF + r) * LS_THREADS + threadIdx.x;
+                if (li < n_t) {
+                    const uint32_t key = (uint32_t)(hit_toa(hv[r]) - base);
+                    S.key[li] = key;
+                    S.pix[li] = hv[r].x;
+                    S.tot[li] = (uint16_t)(hv[r].y & 0xFFFFu);
+                    S.idx[li] = (uint16_t)li;
+                    kmin = key < kmin ? key : kmin;
+                    kmax = key > kmax ? key : kmax;
+                } else {
+                    S.idx[li] = LS_NONE;
+                }
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if (lane == 0) { S.kmin[warp] = kmin; S.kmax[warp] = kmax; }
+        __syncthreads();
+        for (int q = 0; q < LS_WARPS; ++q) { kmin = min(kmin, S.kmin[q]); kmax = max(kmax, S.kmax[q]); }
+        const uint32_t span = kmax - kmin;
+        const int passes = span ? (32 - __clz(span) + RADIX_BITS - 1) / RADIX_BITS : 0;
+
+        for (int pass = 0; pass < passes; ++pass) {
+            const int shift = pass * RADIX_BITS;
+            uint32_t kk[LS_ITEMS];
+            uint16_t ii[LS_ITEMS];
+            uint32_t rr[LS_ITEMS];
+#pragma unroll
+            for (int r = 0; r < LS_ITEMS; ++r) {
+                const uint32_t e = warp * LS_WARP_SPAN + r * 32 + lane;
+                ii[r] = S.idx[e];
+                kk[r] = ii[r] == LS_NONE ? 0 : S.key[ii[r]];
+            }
+            for (int i = threadIdx.x; i < LS_WARPS * RADIX; i += LS_THREADS) (&S.wcnt[0][0])[i] = 0;
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < LS_ITEMS; ++r) {
+                // padding sorts last: digit RADIX-1 in every pass, after all real entries
+                const uint32_t d = ii[r] == LS_NONE ? RADIX - 1 : ((kk[r] - kmin) >> shift) & (RADIX - 1);
+                const uint32_t peers = ls_match_digit(d, 0xffffffffu);
+                const uint32_t rank = __popc(peers & lt);
+                const uint32_t pre = S.wcnt[warp][d];
+                __syncwarp();
+                if (rank == 0) S.wcnt[warp][d] = pre + __popc(peers);
+                __syncwarp();
+                rr[r] = pre + rank;
+                kk[r] = d;   // keep the digit
+            }
+            __syncthreads();
+            {
+                const uint32_t d = threadIdx.x;
+                uint32_t sum = 0;
+#pragma unroll
+                for (int q = 0; q < LS_WARPS; ++q) {
+                    const uint32_t c = S.wcnt[q][d];
+                    S.wcnt[q][d] = sum;
+                    sum += c;
+                }
+                // exclusive scan of the digit totals
+                uint32_t x = sum;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane == 31) S.warp[warp] = x;
+                __syncthreads();
+                uint32_t pre = 0;
+                for (int q = 0; q < warp; ++q) pre += S.warp[q];
+                S.dstart[d] = pre + x - sum;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < LS_ITEMS; ++r) {
+                const uint32_t d = kk[r];
+                S.idx[S.dstart[d] + S.wcnt[warp][d] + rr[r]] = ii[r];
+            }
+            __syncthreads();
+        }
+        for (uint32_t j = threadIdx.x; j < n_t; j += LS_THREADS) {
+            const uint32_t li = S.idx[j];
+            w.keys[0][begin + j] = S.key[li];
+            w.vals[0][begin + j] = begin + li;
+            w.spix[begin + j] = S.pix[li];
+            w.stot[begin + j] = S.tot[li];
+        }
+        __syncthreads();
+    }
+}
+
+// Merge the second half of tile t-1 with the first half of tile t (both
+// sorted by (key, position)), in place.
+struct LmShared {
+    uint32_t key[TILE];
+    uint32_t pos[TILE];
+    uint32_t pix[TILE];
+    uint16_t tot[TILE];
+};
+constexpr int LM_SMEM = (int)sizeof(LmShared);
+
+// (key, position) of a below (key, position) of b
+__device__ __forceinline__ bool lm_below(uint32_t ka, uint32_t pa, uint32_t kb, uint32_t pb) {
+    return ka < kb || (ka == kb && pa < pb);
+}
+
+// Each element's output rank = its index in its own half + the number of
+// elements of the other half that sort before it (binary search; the lanes
+// of a warp search for neighbouring values, so their probes mostly coincide).
+// All loads are issued before any use; outputs are staged in shared memory
+// and written back coalesced.
+__global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
+    extern __shared__ __align__(16) unsigned char lm_raw[];
+    LmShared &S = *reinterpret_cast<LmShared *>(lm_raw);
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        if (t == g.tile0) continue;
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t w0 = begin - TILE / 2;
+        const uint32_t w1 = begin + TILE / 2 < end ? begin + TILE / 2 : end;
+        const uint32_t na = TILE / 2, nw = w1 - w0, nb = nw - na;   // A = [0, na), B = [na, nw)
+        uint32_t rk[LS_ITEMS], rp[LS_ITEMS], rx[LS_ITEMS];
+        uint16_t rt[LS_ITEMS];
+#pragma unroll
+        for (int r = 0; r < LS_ITEMS; ++r) {
+            const uint32_t j = r * LS_THREADS + threadIdx.x;
+            if (j < nw) {
+                rk[r] = w.keys[0][w0 + j];
+                rp[r] = w.vals[0][w0 + j];
+                rx[r] = w.spix[w0 + j];
+                rt[r] = w.stot[w0 + j];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < LS_ITEMS; ++r) {
+            const uint32_t j = r * LS_THREADS + threadIdx.x;
+            if (j < nw) { S.key[j] = rk[r]; S.pos[j] = rp[r]; }
+        }
+        __syncthreads();
+        uint32_t out[LS_ITEMS];
+#pragma unroll
+        for (int r = 0; r < LS_ITEMS; ++r) {
+            const uint32_t j = r * LS_THREADS + threadIdx.x;
+            if (j >= nw) continue;
+            const bool in_a = j < na;
+            uint32_t lo = in_a ? na : 0, hi = in_a ? nw : na;   // search the other half
+            const uint32_t first = lo;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (lm_below(S.key[mid], S.pos[mid], rk[r], rp[r])) lo = mid + 1; else hi = mid;
+            }
+            out[r] = (in_a ? j : j - na) + (lo - first);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < LS_ITEMS; ++r) {
+            const uint32_t j = r * LS_THREADS + threadIdx.x;
+            if (j < nw) {
+                S.key[out[r]] = rk[r];
+                S.pos[out[r]] = rp[r];
+                S.pix[out[r]] = rx[r];
+                S.tot[out[r]] = rt[r];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < LS_ITEMS; ++r) {
+            const uint32_t j = r * LS_THREADS + threadIdx.x;
+            if (j < nw) {
+                w.keys[0][w0 + j] = S.key[j];
+                w.vals[0][w0 + j] = S.pos[j];
+                w.spix[w0 + j] = S.pix[j];
+                w.stot[w0 + j] = S.tot[j];
+            }
+        }
+        __syncthreads();
+        (void)nb;
+    }
+}
+
+// Borders between the sorted runs: mid-tile positions.  Any inversion sends
+// the step to the general radix sort.
+__global__ void __launch_bounds__(256) k_sort_check(Work w) {
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    bool bad = false;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t s = begin + TILE / 2 - 1;
+        if (s + 1 >= end) continue;
+        const uint32_t ka = w.keys[0][s], kb = w.keys[0][s + 1];
+        bad |= ka > kb || (ka == kb && w.vals[0][s] > w.vals[0][s + 1]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+        w.prob->fallback = 1u;
+        w.prob->npasses = w.prob->lsd_passes;
+    }
+}
+
+cudaError_t init_sortfast_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tile_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, LM_SMEM);
+}
+
+void launch_sort_fast(const Work &w, const Launch &L) {
+    k_tile_sort<<<L.grid, LS_THREADS, LS_SMEM, L.stream>>>(w);
+    L.mark("k_tile_sort");
+    k_tile_merge<<<L.grid, LS_THREADS, LM_SMEM, L.stream>>>(w);
+    L.mark("k_tile_merge");
+    k_sort_check<<<L.grid, 256, 0, L.stream>>>(w);
+    L.mark("k_sort_check");
+}
+
+}  // namespace tpc

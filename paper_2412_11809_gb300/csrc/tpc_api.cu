@@ -72,6 +72,7 @@ struct Workspace {
         w.seg = mem.alloc<Seg>(MAX_SEGS, e);
         w.prob = mem.alloc<Prob>(1, e);
         w.tile_seg = mem.alloc<uint32_t>(T, e);
+        w.redo = mem.alloc<uint32_t>(T, e);
         w.keys[0] = mem.alloc<uint32_t>(P, e);
         w.keys[1] = mem.alloc<uint32_t>(P, e);
         w.vals[0] = mem.alloc<uint32_t>(P, e);
@@ -275,6 +276,7 @@ void enqueue_kernels(const Work &w, int nsegs, const Launch &L) {
     launch_setup(w, nsegs, L);
     launch_prepare(w, L);
     launch_seg_finalize(w, L);
+    launch_sort_fast(w, L);
     launch_make_keys(w, L);
     for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
     launch_gather(w, L);
@@ -286,10 +288,10 @@ void enqueue_kernels(const Work &w, int nsegs, const Launch &L) {
 // Run the fixed kernel sequence, from a CUDA graph captured on first use
 // (and re-captured when the workspace or the segment count changes).
 cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, Tracer *tr = nullptr) {
-    const Launch L{grid_of(owner), st};
+    const Launch L{grid_of(owner), st, nullptr, owner->sms};
     if (tr) {   // kernels one by one with an event after each (no graph)
         cudaEventRecord(tr->ev[0], st);
-        enqueue_kernels(ws.w, nsegs, Launch{L.grid, st, tr});
+        enqueue_kernels(ws.w, nsegs, Launch{L.grid, st, tr, owner->sms});
         return cudaGetLastError();
     }
     if (!owner->graph || owner->graph_nsegs != nsegs || owner->graph_pos_cap != ws.pos_cap ||
@@ -304,7 +306,7 @@ cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, 
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            enqueue_kernels(ws.w, nsegs, Launch{L.grid, cap_st});
+            enqueue_kernels(ws.w, nsegs, Launch{L.grid, cap_st, nullptr, owner->sms});
             e = cudaStreamEndCapture(cap_st, &g);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&owner->graph, g, 0);
@@ -611,11 +613,12 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
     if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
     const Work &w = c->ws.w;
     const VarWork &v = c->vs.v;
-    const Launch L{grid_of(c), c->stream, tr};
+    const Launch L{grid_of(c), c->stream, tr, c->sms};
     if (tr) cudaEventRecord(tr->ev[0], c->stream);
     launch_setup(w, 1, L);
     launch_prepare(w, L);
     launch_seg_finalize(w, L);
+    launch_sort_fast(w, L);
     launch_make_keys(w, L);
     for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
     launch_gather(w, L);

@@ -88,10 +88,14 @@ struct Seg {
 struct Prob {
     uint32_t nsegs;
     uint32_t ntiles;
-    uint32_t npasses;      // max over segments; sorted data in buffer npasses % 2
+    uint32_t npasses;      // radix passes run; sorted data in buffer npasses % 2
     uint32_t err;          // ErrBits
     uint32_t tile_cap;
     uint32_t pos_cap;
+    uint32_t fallback;     // the tile sort + merge did not order the input: radix sort
+    uint32_t lsd_passes;   // passes the radix sort needs (max over segments)
+    uint32_t redo_count;   // tiles the table-mode link left to the general link kernel
+    uint32_t pad;
 };
 
 // Work arrays (device), sized for pos_cap positions and tile_cap tiles.
@@ -99,6 +103,7 @@ struct Work {
     Seg *seg;
     Prob *prob;
     uint32_t *tile_seg;        // [tile_cap]
+    uint32_t *redo;            // [tile_cap] tiles handed from table mode to k_tile_link
     uint32_t *keys[2];         // radix ping-pong: ToA - toa_min
     uint32_t *vals[2];         // radix ping-pong: position
     uint32_t *spix;            // sorted positions: x | y << 16
@@ -224,6 +229,7 @@ struct Launch {
     int grid;          // persistent CTAs
     cudaStream_t stream;
     Tracer *tr = nullptr;
+    int sms = 0;       // SM count (one CTA per SM for the shared-memory-heavy kernels)
     void mark(const char *name) const { if (tr) tr->mark(name, stream); }
 };
 
@@ -232,6 +238,8 @@ void launch_setup(const Work &w, int nsegs, const Launch &L);
 void launch_prepare(const Work &w, const Launch &L);
 void launch_seg_finalize(const Work &w, const Launch &L);
 void launch_make_keys(const Work &w, const Launch &L);
+void launch_sort_fast(const Work &w, const Launch &L);
+cudaError_t init_sortfast_attributes();
 void launch_radix_pass(const Work &w, int pass, const Launch &L);
 void launch_gather(const Work &w, const Launch &L);
 void launch_link(const Work &w, const Launch &L);          // tile + border + flatten
