@@ -21,51 +21,66 @@ namespace tpc {
 constexpr int ACC_THREADS = 256;
 constexpr int ACC_SPAN = 2048;                    // sorted positions per pass
 constexpr int ACC_ITEMS = ACC_SPAN / ACC_THREADS;
-constexpr int ACC_SMEM = 8 * ACC_SPAN * (int)sizeof(uint32_t);
+constexpr int ACC_SMEM = 6 * ACC_SPAN * (int)sizeof(uint32_t) + 2 * ACC_SPAN * (int)sizeof(unsigned long long);
 
-// Features in (ToA, position) order, where a cluster's hits sit close
-// together: each pass over ACC_SPAN sorted positions sums into shared-memory
-// slots of the roots that lie inside the span (a root precedes all of its
-// cluster's hits), then adds one partial per such root to the global slots;
-// hits whose root lies before the span go straight to the global slots.
-// Sums of ToT*x and ToT*y are kept as 16-bit halves so 32-bit shared
-// atomics cannot overflow (span < 2^16 hits, ToT*x < 2^32).
+// Roots and features in (ToA, position) order, where a cluster's hits sit
+// close together.  Each pass over ACC_SPAN sorted positions finds every
+// position's root (the global forest is shallow after the tile links),
+// records it by input position for the label pass, and sums into shared-
+// memory slots of the roots inside the span (a root precedes its cluster's
+// hits); hits of one cluster within a warp are combined first (match.any +
+// redux), so a burst of one track does not serialise on one slot.  One
+// partial per root then goes to the global slots; hits whose root lies
+// before the span go there directly.  The global slots of tile roots were
+// zeroed by the tile-link kernels.
 __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
-    extern __shared__ uint32_t acc[];
-    uint32_t *a_size = acc, *a_tot = acc + ACC_SPAN, *a_wxh = acc + 2 * ACC_SPAN,
-             *a_wxl = acc + 3 * ACC_SPAN, *a_wyh = acc + 4 * ACC_SPAN, *a_wyl = acc + 5 * ACC_SPAN,
-             *a_min = acc + 6 * ACC_SPAN, *a_max = acc + 7 * ACC_SPAN;
+    extern __shared__ __align__(16) unsigned char acc_raw[];
+    unsigned long long *a_wx = reinterpret_cast<unsigned long long *>(acc_raw);
+    unsigned long long *a_wy = a_wx + ACC_SPAN;
+    uint32_t *a_size = reinterpret_cast<uint32_t *>(a_wy + ACC_SPAN), *a_tot = a_size + ACC_SPAN,
+             *a_min = a_size + 2 * ACC_SPAN, *a_max = a_size + 3 * ACC_SPAN;
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
     const uint32_t *sidx = w.vals[sorted_sel(P)];
-    const uint32_t *sroot = w.keys[sorted_sel(P) ^ 1u];   // written by k_flatten
+    const int lane = threadIdx.x & 31;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         for (uint32_t b = begin; b < end; b += ACC_SPAN) {
             const uint32_t e = b + ACC_SPAN < end ? b + ACC_SPAN : end;
-            uint32_t rr[ACC_ITEMS];
-            uint32_t px[ACC_ITEMS], tt[ACC_ITEMS], kk[ACC_ITEMS], ps[ACC_ITEMS];
+            uint32_t rr[ACC_ITEMS], px[ACC_ITEMS], tt[ACC_ITEMS], kk[ACC_ITEMS], ps[ACC_ITEMS];
 #pragma unroll
             for (int q = 0; q < ACC_ITEMS; ++q) {   // every load in flight before any use
                 const uint32_t s = b + q * ACC_THREADS + threadIdx.x;
                 if (s < e) {
-                    rr[q] = sroot[s];
+                    rr[q] = w.parent[s];
                     px[q] = w.spix[s];
                     tt[q] = w.stot[s];
                     kk[q] = skey[s];
                     ps[q] = sidx[s];
-                } else {
-                    rr[q] = 0;
                 }
+            }
+            uint32_t p2[ACC_ITEMS];
+#pragma unroll
+            for (int q = 0; q < ACC_ITEMS; ++q) {   // second hop for every item at once
+                const uint32_t s = b + q * ACC_THREADS + threadIdx.x;
+                p2[q] = s < e && rr[q] != s ? w.parent[rr[q]] : rr[q];
             }
 #pragma unroll
             for (int q = 0; q < ACC_ITEMS; ++q) {
-                const uint32_t k = q * ACC_THREADS + threadIdx.x;
-                if (b + k < e && rr[q] == b + k) {
-                    a_size[k] = a_tot[k] = a_wxh[k] = a_wxl[k] = a_wyh[k] = a_wyl[k] = 0;
+                const uint32_t s = b + q * ACC_THREADS + threadIdx.x;
+                if (s >= e) continue;
+                // parent[s] is s's tile root; that root is global unless a border
+                // link hooked it (then follow the rest of the path)
+                const uint32_t r = p2[q] == rr[q] ? rr[q] : gfind(w.parent, p2[q]);
+                rr[q] = r;
+                w.root_of[ps[q]] = r;
+                if (r == s) {
+                    const uint32_t k = s - b;
+                    a_size[k] = a_tot[k] = 0;
+                    a_wx[k] = a_wy[k] = 0;
                     a_min[k] = 0xFFFFFFFFu;
                     a_max[k] = 0;
                 }
@@ -74,27 +89,41 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
 #pragma unroll
             for (int q = 0; q < ACC_ITEMS; ++q) {
                 const uint32_t s = b + q * ACC_THREADS + threadIdx.x;
-                if (s >= e) continue;
-                const uint32_t r = rr[q];
-                const uint32_t pix = px[q], tot = tt[q], key = kk[q], pos = ps[q];
-                const uint32_t wx = tot * (pix & 0xFFFFu), wy = tot * (pix >> 16);
+                const bool valid = s < e;
+                const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+                if (!valid) continue;
+                const uint32_t r = rr[q], pix = px[q], tot = tt[q];
+                const uint32_t peers = __match_any_sync(vmask, r);
+                const uint32_t cnt = __popc(peers);
+                uint32_t sum_tot = tot, mn = ps[q], mx = kk[q];
+                unsigned long long wx = (unsigned long long)tot * (pix & 0xFFFFu);
+                unsigned long long wy = (unsigned long long)tot * (pix >> 16);
+                if (cnt > 1) {   // combine this cluster's hits of the warp
+                    const uint32_t wx32 = tot * (pix & 0xFFFFu), wy32 = tot * (pix >> 16);
+                    sum_tot = __reduce_add_sync(peers, tot);
+                    wx = ((unsigned long long)__reduce_add_sync(peers, wx32 >> 16) << 16) +
+                         __reduce_add_sync(peers, wx32 & 0xFFFFu);
+                    wy = ((unsigned long long)__reduce_add_sync(peers, wy32 >> 16) << 16) +
+                         __reduce_add_sync(peers, wy32 & 0xFFFFu);
+                    mn = __reduce_min_sync(peers, mn);
+                    mx = __reduce_max_sync(peers, mx);
+                }
+                if (lane != __ffs(peers) - 1) continue;
                 if (r >= b) {
                     const uint32_t k = r - b;
-                    atomicAdd(&a_size[k], 1u);
-                    atomicAdd(&a_tot[k], tot);
-                    atomicAdd(&a_wxh[k], wx >> 16);
-                    atomicAdd(&a_wxl[k], wx & 0xFFFFu);
-                    atomicAdd(&a_wyh[k], wy >> 16);
-                    atomicAdd(&a_wyl[k], wy & 0xFFFFu);
-                    atomicMin(&a_min[k], pos);
-                    atomicMax(&a_max[k], key);
+                    atomicAdd(&a_size[k], cnt);
+                    atomicAdd(&a_tot[k], sum_tot);
+                    atomicAdd(&a_wx[k], wx);
+                    atomicAdd(&a_wy[k], wy);
+                    atomicMin(&a_min[k], mn);
+                    atomicMax(&a_max[k], mx);
                 } else {
-                    atomicAdd(&w.slot_size[r], 1u);
-                    atomicAdd(&w.slot_tot[r], (unsigned long long)tot);
-                    atomicAdd(&w.slot_wx[r], (unsigned long long)wx);
-                    atomicAdd(&w.slot_wy[r], (unsigned long long)wy);
-                    atomicMin(&w.slot_min[r], pos);
-                    atomicMax(&w.slot_maxkey[r], key);
+                    atomicAdd(&w.slot_size[r], cnt);
+                    atomicAdd(&w.slot_tot[r], (unsigned long long)sum_tot);
+                    atomicAdd(&w.slot_wx[r], wx);
+                    atomicAdd(&w.slot_wy[r], wy);
+                    atomicMin(&w.slot_min[r], mn);
+                    atomicMax(&w.slot_maxkey[r], mx);
                 }
             }
             __syncthreads();
@@ -105,8 +134,8 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
                 if (r < e && rr[q] == r) {
                     atomicAdd(&w.slot_size[r], a_size[k]);
                     atomicAdd(&w.slot_tot[r], (unsigned long long)a_tot[k]);
-                    atomicAdd(&w.slot_wx[r], ((unsigned long long)a_wxh[k] << 16) + a_wxl[k]);
-                    atomicAdd(&w.slot_wy[r], ((unsigned long long)a_wyh[k] << 16) + a_wyl[k]);
+                    atomicAdd(&w.slot_wx[r], a_wx[k]);
+                    atomicAdd(&w.slot_wy[r], a_wy[k]);
                     atomicMin(&w.slot_min[r], a_min[k]);
                     atomicMax(&w.slot_maxkey[r], a_max[k]);
                 }

@@ -300,8 +300,11 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
             atomicMin(&s_min[r], k);
         }
         __syncthreads();
-        for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS)
-            w.parent[begin + k] = begin + s_min[s_root[k]];
+        for (uint32_t k = threadIdx.x; k < n_t; k += LINK_THREADS) {
+            const uint32_t m = s_min[s_root[k]];
+            w.parent[begin + k] = begin + m;
+            if (m == k) init_slot(w, begin + k);
+        }
         __syncthreads();
     }
 }
@@ -474,7 +477,9 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
         for (int q = 0; q < ITEMS; ++q) {
             const uint32_t k = q * TAB_THREADS + threadIdx.x;
             if (k < n_t) {
-                w.parent[begin + k] = begin + vpar[k];
+                const uint32_t r = vpar[k];
+                w.parent[begin + k] = begin + r;
+                if (r == k) init_slot(w, begin + k);
                 S.tab[tab_pid(pv[q], W)] = TAB_NONE;   // reset only what this tile touched
             }
         }
@@ -627,9 +632,9 @@ void launch_flatten(const Work &w, const Launch &L) {
     L.mark("k_flatten");
 }
 
+// Tile links and border links; roots are found by k_accumulate.
 void launch_link(const Work &w, const Launch &L) {
     launch_tile_border(w, L);
-    launch_flatten(w, L);
 }
 
 }  // namespace tpc

@@ -28,6 +28,8 @@ constexpr int LS_WARPS = LS_THREADS / 32;
 constexpr int LS_ITEMS = TILE / LS_THREADS;    // 16
 constexpr int LS_WARP_SPAN = TILE / LS_WARPS;  // 512
 constexpr uint16_t LS_NONE = 0xFFFFu;
+constexpr int LS_BITS = 9;                     // digit width of the in-tile sort
+constexpr int LS_RADIX = 1 << LS_BITS;         // 512 buckets: a 17-bit tile span in 2 passes
 
 __device__ __forceinline__ uint32_t ls_lanemask_lt() {
     uint32_t m;
@@ -38,7 +40,7 @@ __device__ __forceinline__ uint32_t ls_lanemask_lt() {
 __device__ __forceinline__ uint32_t ls_match_digit(uint32_t d, uint32_t vmask) {
     uint32_t peers = vmask;
 #pragma unroll
-    for (int b = 0; b < RADIX_BITS; ++b) {
+    for (int b = 0; b < LS_BITS; ++b) {
         const uint32_t bit = (d >> b) & 1u;
         const uint32_t bal = __ballot_sync(0xffffffffu, bit);
         peers &= bit ? bal : ~bal;
@@ -51,8 +53,8 @@ struct LsShared {
     uint32_t pix[TILE];
     uint16_t tot[TILE];
     uint16_t idx[TILE];          // local input index of the element at each rank
-    uint32_t wcnt[LS_WARPS][RADIX];
-    uint32_t dstart[RADIX];
+    uint32_t wcnt[LS_WARPS][LS_RADIX];
+    uint32_t dstart[LS_RADIX];
     uint32_t warp[32];
     uint32_t kmin[LS_WARPS], kmax[LS_WARPS];
 };
@@ -107,10 +109,10 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
         __syncthreads();
         for (int q = 0; q < LS_WARPS; ++q) { kmin = min(kmin, S.kmin[q]); kmax = max(kmax, S.kmax[q]); }
         const uint32_t span = kmax - kmin;
-        const int passes = span ? (32 - __clz(span) + RADIX_BITS - 1) / RADIX_BITS : 0;
+        const int passes = span ? (32 - __clz(span) + LS_BITS - 1) / LS_BITS : 0;
 
         for (int pass = 0; pass < passes; ++pass) {
-            const int shift = pass * RADIX_BITS;
+            const int shift = pass * LS_BITS;
             uint32_t kk[LS_ITEMS];
             uint16_t ii[LS_ITEMS];
             uint32_t rr[LS_ITEMS];
@@ -120,12 +122,12 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
                 ii[r] = S.idx[e];
                 kk[r] = ii[r] == LS_NONE ? 0 : S.key[ii[r]];
             }
-            for (int i = threadIdx.x; i < LS_WARPS * RADIX; i += LS_THREADS) (&S.wcnt[0][0])[i] = 0;
+            for (int i = threadIdx.x; i < LS_WARPS * LS_RADIX; i += LS_THREADS) (&S.wcnt[0][0])[i] = 0;
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < LS_ITEMS; ++r) {
                 // padding sorts last: digit RADIX-1 in every pass, after all real entries
-                const uint32_t d = ii[r] == LS_NONE ? RADIX - 1 : ((kk[r] - kmin) >> shift) & (RADIX - 1);
+                const uint32_t d = ii[r] == LS_NONE ? LS_RADIX - 1 : ((kk[r] - kmin) >> shift) & (LS_RADIX - 1);
                 const uint32_t peers = ls_match_digit(d, 0xffffffffu);
                 const uint32_t rank = __popc(peers & lt);
                 const uint32_t pre = S.wcnt[warp][d];
@@ -136,17 +138,23 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
                 kk[r] = d;   // keep the digit
             }
             __syncthreads();
-            {
-                const uint32_t d = threadIdx.x;
-                uint32_t sum = 0;
+            {   // per digit: prefix over warps; then exclusive scan of the digit totals
+                // (LS_RADIX / LS_THREADS = 2 consecutive digits per thread)
+                const uint32_t d0 = 2 * threadIdx.x;
+                uint32_t tot2[2];
 #pragma unroll
-                for (int q = 0; q < LS_WARPS; ++q) {
-                    const uint32_t c = S.wcnt[q][d];
-                    S.wcnt[q][d] = sum;
-                    sum += c;
+                for (int u = 0; u < 2; ++u) {
+                    uint32_t sum = 0;
+#pragma unroll
+                    for (int q = 0; q < LS_WARPS; ++q) {
+                        const uint32_t c = S.wcnt[q][d0 + u];
+                        S.wcnt[q][d0 + u] = sum;
+                        sum += c;
+                    }
+                    tot2[u] = sum;
                 }
-                // exclusive scan of the digit totals
-                uint32_t x = sum;
+                const uint32_t both = tot2[0] + tot2[1];
+                uint32_t x = both;
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                     if (lane >= o) x += y;
@@ -155,7 +163,8 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
                 __syncthreads();
                 uint32_t pre = 0;
                 for (int q = 0; q < warp; ++q) pre += S.warp[q];
-                S.dstart[d] = pre + x - sum;
+                S.dstart[d0] = pre + x - both;
+                S.dstart[d0 + 1] = pre + x - both + tot2[0];
             }
             __syncthreads();
 #pragma unroll

@@ -150,6 +150,16 @@ __device__ __forceinline__ uint64_t gidx_of(const Seg &s, uint32_t local) {
 
 __device__ __forceinline__ uint32_t sorted_sel(const Prob &p) { return p.npasses & 1u; }
 
+// Zero the feature slot of root r (a tile root; every global root is one).
+__device__ __forceinline__ void init_slot(const Work &w, uint32_t r) {
+    w.slot_size[r] = 0;
+    w.slot_min[r] = 0xFFFFFFFFu;
+    w.slot_maxkey[r] = 0;
+    w.slot_tot[r] = 0;
+    w.slot_wx[r] = 0;
+    w.slot_wy[r] = 0;
+}
+
 // Union-find on global memory over sorted positions.  Roots are the smaller
 // position (hook the larger root under the smaller, Jaiganesh & Burtscher,
 // "A high-performance connected components implementation for GPUs", 2018);
