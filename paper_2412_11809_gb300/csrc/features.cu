@@ -18,7 +18,7 @@
 
 namespace tpc {
 
-constexpr int ACC_THREADS = 256;
+constexpr int ACC_THREADS = 512;
 constexpr int ACC_SPAN = 2048;                    // sorted positions per pass
 constexpr int ACC_ITEMS = ACC_SPAN / ACC_THREADS;
 constexpr int ACC_SMEM = 6 * ACC_SPAN * (int)sizeof(uint32_t) + 2 * ACC_SPAN * (int)sizeof(unsigned long long);

@@ -379,7 +379,6 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
     for (uint32_t i = threadIdx.x; i < TAB_PIXELS / 2; i += TAB_THREADS)
         reinterpret_cast<uint32_t *>(S.tab)[i] = 0xFFFFFFFFu;
     __syncthreads();
@@ -408,11 +407,15 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             }
         }
         __syncthreads();
-        // neighbour walk: first earlier neighbour = parent, the rest = edges
+        // neighbour walk: smallest earlier neighbour = parent, the others =
+        // edges, gathered in registers and appended warp by warp (ballots)
+        constexpr int CAND = 6;
+        const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
         for (int q = 0; q < ITEMS; ++q) {
             const uint32_t k = q * TAB_THREADS + threadIdx.x;
-            uint32_t parent = k;
+            uint32_t parent = k, cand[CAND];
+            int nc = 0;
             if (k < n_t) {
                 const uint32_t key = kv[q];
                 const int x = (int)(pv[q] & 0xFFFFu), y = (int)(pv[q] >> 16);
@@ -426,17 +429,30 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                         int steps = 0;
                         for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps) {
                             if (j >= k || key - S.key[j] > dt) continue;
-                            if (parent == k) {
-                                parent = j;
-                            } else {
+                            uint32_t other = j;
+                            if (parent == k) { parent = j; continue; }
+                            if (j < parent) { other = parent; parent = j; }
+                            if (nc < CAND) {
+                                cand[nc++] = other;
+                            } else {   // rare: straight to the edge list
                                 const uint32_t slot = atomicAdd(&S.nedges, 1u);
-                                if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | j;
+                                if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | other;
                             }
                         }
                         if (j != TAB_NONE) S.overflow = 1;
                     }
                 }
                 S.par[k] = parent;
+            }
+            const uint32_t most = __reduce_max_sync(0xffffffffu, (uint32_t)nc);
+            for (uint32_t c = 0; c < most; ++c) {
+                const bool has = (int)c < nc;
+                const uint32_t m = __ballot_sync(0xffffffffu, has);
+                uint32_t slot0 = 0;
+                if (lane == 0) slot0 = atomicAdd(&S.nedges, (uint32_t)__popc(m));
+                slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+                const uint32_t slot = slot0 + __popc(m & lt_mask);
+                if (has && slot < TAB_EDGES) S.edges[slot] = (k << 16) | cand[c];
             }
         }
         __syncthreads();
@@ -455,8 +471,9 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
         }
         const uint32_t ne = S.nedges;
         while (true) {
+            // flatten: every rank jumps to its root (parents only move rootwards)
 #pragma unroll
-            for (int q = 0; q < ITEMS; ++q) {   // flatten
+            for (int q = 0; q < ITEMS; ++q) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
                 if (k < n_t) vpar[k] = tab_root(vpar, k);
             }
@@ -472,7 +489,6 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             }
             if (!__syncthreads_or(hooked)) break;
         }
-        (void)lt;
 #pragma unroll
         for (int q = 0; q < ITEMS; ++q) {
             const uint32_t k = q * TAB_THREADS + threadIdx.x;
