@@ -200,14 +200,21 @@ __device__ __forceinline__ bool lm_below(uint32_t ka, uint32_t pa, uint32_t kb, 
     return ka < kb || (ka == kb && pa < pb);
 }
 
-// Each element's output rank = its index in its own half + the number of
-// elements of the other half that sort before it (binary search; the lanes
-// of a warp search for neighbouring values, so their probes mostly coincide).
-// All loads are issued before any use; outputs are staged in shared memory
-// and written back coalesced.
+// Only the part of the window where the two halves interleave moves: A's
+// elements above B's first and B's elements below A's last.  Keys and
+// positions of a band of MERGE_BAND entries on each side of the border are
+// read first to locate that overlap (the whole window when the overlap
+// reaches the band's edge); pixels and ToTs are read, and everything
+// written back, for the overlap only.  Each moving element's output rank =
+// its index in its own part + the number of the other part's elements that
+// sort before it (binary search; the lanes of a warp search for
+// neighbouring values, so their probes mostly coincide).
+constexpr uint32_t MERGE_BAND = TILE / 4;
+
 __global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
     extern __shared__ __align__(16) unsigned char lm_raw[];
     LmShared &S = *reinterpret_cast<LmShared *>(lm_raw);
+    __shared__ uint32_t s_cut[2];
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
@@ -215,65 +222,86 @@ __global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
         if (t == g.tile0) continue;
         uint32_t begin, end;
         tile_range(g, t, begin, end);
-        const uint32_t w0 = begin - TILE / 2;
-        const uint32_t w1 = begin + TILE / 2 < end ? begin + TILE / 2 : end;
-        const uint32_t na = TILE / 2, nw = w1 - w0, nb = nw - na;   // A = [0, na), B = [na, nw)
-        uint32_t rk[LS_ITEMS], rp[LS_ITEMS], rx[LS_ITEMS];
-        uint16_t rt[LS_ITEMS];
-#pragma unroll
-        for (int r = 0; r < LS_ITEMS; ++r) {
-            const uint32_t j = r * LS_THREADS + threadIdx.x;
-            if (j < nw) {
-                rk[r] = w.keys[0][w0 + j];
-                rp[r] = w.vals[0][w0 + j];
-                rx[r] = w.spix[w0 + j];
-                rt[r] = w.stot[w0 + j];
+        const uint32_t nb_all = end - begin < TILE / 2 ? end - begin : TILE / 2;
+        {   // already in order across the border?
+            const uint32_t ka = w.keys[0][begin - 1], kb = w.keys[0][begin];
+            if (ka < kb || (ka == kb && w.vals[0][begin - 1] < w.vals[0][begin])) continue;
+        }
+        for (uint32_t band = MERGE_BAND;; band = TILE / 2) {
+            const uint32_t na = band, nb = band < nb_all ? band : nb_all;
+            const uint32_t a0 = begin - na;   // A = [a0, begin), B = [begin, begin + nb)
+            for (uint32_t j = threadIdx.x; j < na + nb; j += LS_THREADS) {
+                S.key[j] = w.keys[0][a0 + j];
+                S.pos[j] = w.vals[0][a0 + j];
             }
-        }
-#pragma unroll
-        for (int r = 0; r < LS_ITEMS; ++r) {
-            const uint32_t j = r * LS_THREADS + threadIdx.x;
-            if (j < nw) { S.key[j] = rk[r]; S.pos[j] = rp[r]; }
-        }
-        __syncthreads();
-        uint32_t out[LS_ITEMS];
-#pragma unroll
-        for (int r = 0; r < LS_ITEMS; ++r) {
-            const uint32_t j = r * LS_THREADS + threadIdx.x;
-            if (j >= nw) continue;
-            const bool in_a = j < na;
-            uint32_t lo = in_a ? na : 0, hi = in_a ? nw : na;   // search the other half
-            const uint32_t first = lo;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (lm_below(S.key[mid], S.pos[mid], rk[r], rp[r])) lo = mid + 1; else hi = mid;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                // ia = A elements below B[0]; ib = B elements below A[last]
+                uint32_t lo = 0, hi = na;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (lm_below(S.key[mid], S.pos[mid], S.key[na], S.pos[na])) lo = mid + 1; else hi = mid;
+                }
+                s_cut[0] = lo;
+                lo = na; hi = na + nb;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (lm_below(S.key[mid], S.pos[mid], S.key[na - 1], S.pos[na - 1])) lo = mid + 1; else hi = mid;
+                }
+                s_cut[1] = lo - na;
             }
-            out[r] = (in_a ? j : j - na) + (lo - first);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < LS_ITEMS; ++r) {
-            const uint32_t j = r * LS_THREADS + threadIdx.x;
-            if (j < nw) {
-                S.key[out[r]] = rk[r];
-                S.pos[out[r]] = rp[r];
-                S.pix[out[r]] = rx[r];
-                S.tot[out[r]] = rt[r];
+            __syncthreads();
+            const uint32_t ia = s_cut[0], ib = s_cut[1];
+            const bool contained = (ia > 0 || na == TILE / 2) && (ib < nb || nb == nb_all);
+            if (!contained && band != TILE / 2) {
+                __syncthreads();
+                continue;   // overlap wider than the band: take the whole window
             }
-        }
-        __syncthreads();
+            // moving part: A[ia, na) and B[0, ib), output positions a0 + ia ...
+            const uint32_t ma = na - ia, m = ma + ib;
+            uint32_t rk[LS_ITEMS], rp[LS_ITEMS], rx[LS_ITEMS], out[LS_ITEMS];
+            uint16_t rt[LS_ITEMS];
 #pragma unroll
-        for (int r = 0; r < LS_ITEMS; ++r) {
-            const uint32_t j = r * LS_THREADS + threadIdx.x;
-            if (j < nw) {
-                w.keys[0][w0 + j] = S.key[j];
-                w.vals[0][w0 + j] = S.pos[j];
-                w.spix[w0 + j] = S.pix[j];
-                w.stot[w0 + j] = S.tot[j];
+            for (int r = 0; r < LS_ITEMS; ++r) {
+                const uint32_t j = r * LS_THREADS + threadIdx.x;
+                if (j < m) {
+                    const uint32_t src = j < ma ? ia + j : na + (j - ma);   // index in S
+                    rk[r] = S.key[src];
+                    rp[r] = S.pos[src];
+                    rx[r] = w.spix[a0 + src];
+                    rt[r] = w.stot[a0 + src];
+                    const bool in_a = j < ma;
+                    uint32_t lo = in_a ? na : ia, hi = in_a ? na + ib : na;   // the other part
+                    const uint32_t first = lo;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (lm_below(S.key[mid], S.pos[mid], rk[r], rp[r])) lo = mid + 1; else hi = mid;
+                    }
+                    out[r] = (in_a ? j : j - ma) + (lo - first);
+                }
             }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < LS_ITEMS; ++r) {
+                const uint32_t j = r * LS_THREADS + threadIdx.x;
+                if (j < m) {
+                    S.key[out[r]] = rk[r];
+                    S.pos[out[r]] = rp[r];
+                    S.pix[out[r]] = rx[r];
+                    S.tot[out[r]] = rt[r];
+                }
+            }
+            __syncthreads();
+            const uint32_t o0 = a0 + ia;
+            for (uint32_t j = threadIdx.x; j < m; j += LS_THREADS) {
+                w.keys[0][o0 + j] = S.key[j];
+                w.vals[0][o0 + j] = S.pos[j];
+                w.spix[o0 + j] = S.pix[j];
+                w.stot[o0 + j] = S.tot[j];
+            }
+            __syncthreads();
+            break;
         }
-        __syncthreads();
-        (void)nb;
     }
 }
 
