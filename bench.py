@@ -46,9 +46,20 @@ HIT_DTYPE_NP = np.dtype([("x", "<u2"), ("y", "<u2"), ("tot", "<u2"), ("reserved"
 # (records 16 B, keys/positions/pixels/parents 4 B, labels 8 B); the cluster
 # record bytes are charged per cluster.  Used for the dominant kernel's roofline.
 KERNEL_BYTES_PER_HIT = {
-    "k_prepare": 16, "k_make_keys": 16 + 8, "k_gather": 4 + 16 + 4,
-    "k_tile_link": 4 + 4 + 4, "k_flatten": 4 + 4 + 4, "k_accumulate": 4 + 16,
-    "k_labels": 4 + 8, "k_border_link": 0,
+    # load + validate: the 16-byte record
+    "k_prepare": 16,
+    # in-tile sort: read the record; write key, position, pixel (4 each), ToT (2)
+    "k_tile_sort": 16 + 14,
+    # table link: read key and pixel, write the parent
+    "k_tile_link_table": 4 + 4 + 4,
+    "k_tile_link": 4 + 4 + 4,
+    # features: read parent, pixel, ToT, key, position; write root by input position
+    "k_accumulate": 4 + 4 + 2 + 4 + 4 + 4,
+    # labels: read the root, write the 8-byte label
+    "k_labels": 4 + 8,
+    # general sort (fallback only)
+    "k_make_keys": 16 + 8, "k_gather": 4 + 16 + 4, "k_flatten": 4 + 4 + 4,
+    "k_border_link": 0,
 }
 for _p in range(4):
     KERNEL_BYTES_PER_HIT[f"k_radix_upsweep{_p}"] = 4

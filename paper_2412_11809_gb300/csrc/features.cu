@@ -21,7 +21,7 @@ namespace tpc {
 constexpr int ACC_THREADS = 512;
 constexpr int ACC_SPAN = 2048;                    // sorted positions per pass
 constexpr int ACC_ITEMS = ACC_SPAN / ACC_THREADS;
-constexpr int ACC_SMEM = 6 * ACC_SPAN * (int)sizeof(uint32_t) + 2 * ACC_SPAN * (int)sizeof(unsigned long long);
+constexpr int ACC_SMEM = 4 * ACC_SPAN * (int)sizeof(uint32_t) + 2 * ACC_SPAN * (int)sizeof(unsigned long long);
 
 // Roots and features in (ToA, position) order, where a cluster's hits sit
 // close together.  Each pass over ACC_SPAN sorted positions finds every
@@ -33,7 +33,7 @@ constexpr int ACC_SMEM = 6 * ACC_SPAN * (int)sizeof(uint32_t) + 2 * ACC_SPAN * (
 // partial per root then goes to the global slots; hits whose root lies
 // before the span go there directly.  The global slots of tile roots were
 // zeroed by the tile-link kernels.
-__global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
+__global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
     extern __shared__ __align__(16) unsigned char acc_raw[];
     unsigned long long *a_wx = reinterpret_cast<unsigned long long *>(acc_raw);
     unsigned long long *a_wy = a_wx + ACC_SPAN;
@@ -118,12 +118,13 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
                     atomicMin(&a_min[k], mn);
                     atomicMax(&a_max[k], mx);
                 } else {
-                    atomicAdd(&w.slot_size[r], cnt);
-                    atomicAdd(&w.slot_tot[r], (unsigned long long)sum_tot);
-                    atomicAdd(&w.slot_wx[r], wx);
-                    atomicAdd(&w.slot_wy[r], wy);
-                    atomicMin(&w.slot_min[r], mn);
-                    atomicMax(&w.slot_maxkey[r], mx);
+                    Slot &sl = w.slot[r];
+                    atomicAdd(&sl.size, cnt);
+                    atomicAdd(&sl.tot, (unsigned long long)sum_tot);
+                    atomicAdd(&sl.wx, wx);
+                    atomicAdd(&sl.wy, wy);
+                    atomicMin(&sl.min, mn);
+                    atomicMax(&sl.maxkey, mx);
                 }
             }
             __syncthreads();
@@ -132,12 +133,13 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(Work w) {
                 const uint32_t k = q * ACC_THREADS + threadIdx.x;
                 const uint32_t r = b + k;
                 if (r < e && rr[q] == r) {
-                    atomicAdd(&w.slot_size[r], a_size[k]);
-                    atomicAdd(&w.slot_tot[r], (unsigned long long)a_tot[k]);
-                    atomicAdd(&w.slot_wx[r], a_wx[k]);
-                    atomicAdd(&w.slot_wy[r], a_wy[k]);
-                    atomicMin(&w.slot_min[r], a_min[k]);
-                    atomicMax(&w.slot_maxkey[r], a_max[k]);
+                    Slot &sl = w.slot[r];
+                    atomicAdd(&sl.size, a_size[k]);
+                    atomicAdd(&sl.tot, (unsigned long long)a_tot[k]);
+                    atomicAdd(&sl.wx, a_wx[k]);
+                    atomicAdd(&sl.wy, a_wy[k]);
+                    atomicMin(&sl.min, a_min[k]);
+                    atomicMax(&sl.maxkey, a_max[k]);
                 }
             }
             __syncthreads();
@@ -163,39 +165,43 @@ __global__ void __launch_bounds__(256) k_labels(Work w) {
         if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
         __syncthreads();
         uint32_t c_label = 0, c_closed = 0;
-        constexpr int ITEMS = TILE / 256;
-        uint32_t rr[ITEMS], ll[ITEMS], mk[ITEMS];
+        constexpr int PARTS = 4;                 // fewer registers, more resident warps
+        constexpr int ITEMS = TILE / 256 / PARTS;
+        for (int part = 0; part < PARTS; ++part) {
+            const uint32_t base = begin + part * (ITEMS * 256);
+            uint32_t rr[ITEMS], ll[ITEMS], mk[ITEMS];
 #pragma unroll
-        for (int q = 0; q < ITEMS; ++q) {
-            const uint32_t pos = begin + q * 256 + threadIdx.x;
-            rr[q] = pos < end ? w.root_of[pos] : 0;
-        }
-#pragma unroll
-        for (int q = 0; q < ITEMS; ++q) {
-            const uint32_t pos = begin + q * 256 + threadIdx.x;
-            ll[q] = pos < end ? w.slot_min[rr[q]] : 0;
-            mk[q] = pos < end && g.close_mode == CLOSE_WM ? w.slot_maxkey[rr[q]] : 0;
-        }
-#pragma unroll
-        for (int q = 0; q < ITEMS; ++q) {
-            const uint32_t pos = begin + q * 256 + threadIdx.x;
-            const bool valid = pos < end;
-            bool is_label = false, closed = false;
-            if (valid) {
-                const uint32_t l = ll[q];
-                closed = cluster_closed(g, mk[q]);
-                is_label = closed && l == pos;
-                const uint64_t lab = gidx_of(g, l - g.off);
-                if (direct) g.out_labels[pos - g.off] = lab;
-                else w.lab_tmp[pos] = lab;
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t pos = base + q * 256 + threadIdx.x;
+                rr[q] = pos < end ? w.root_of[pos] : 0;
             }
-            const uint32_t bl = __ballot_sync(0xffffffffu, is_label);
-            const uint32_t bc = __ballot_sync(0xffffffffu, valid && closed);
-            if (lane == 0) {
-                w.flag_label[pos >> 5] = bl;
-                w.flag_closed[pos >> 5] = bc;
-                c_label += __popc(bl);
-                c_closed += __popc(bc);
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t pos = base + q * 256 + threadIdx.x;
+                ll[q] = pos < end ? w.slot[rr[q]].min : 0;
+                mk[q] = pos < end && g.close_mode == CLOSE_WM ? w.slot[rr[q]].maxkey : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t pos = base + q * 256 + threadIdx.x;
+                const bool valid = pos < end;
+                bool is_label = false, closed = false;
+                if (valid) {
+                    const uint32_t l = ll[q];
+                    closed = cluster_closed(g, mk[q]);
+                    is_label = closed && l == pos;
+                    const uint64_t lab = gidx_of(g, l - g.off);
+                    if (direct) g.out_labels[pos - g.off] = lab;
+                    else w.lab_tmp[pos] = lab;
+                }
+                const uint32_t bl = __ballot_sync(0xffffffffu, is_label);
+                const uint32_t bc = __ballot_sync(0xffffffffu, valid && closed);
+                if (lane == 0) {
+                    w.flag_label[pos >> 5] = bl;
+                    w.flag_closed[pos >> 5] = bc;
+                    c_label += __popc(bl);
+                    c_closed += __popc(bc);
+                }
             }
         }
         if (lane == 0) {
@@ -282,12 +288,13 @@ __global__ void __launch_bounds__(TILE_WORDS) k_records(Work w) {
             if (ord < g.out_cap) {
                 tpc_cluster rec;
                 rec.label = gidx_of(g, pos - g.off);
-                rec.size = (int64_t)w.slot_size[r];
-                rec.sum_tot = (int64_t)w.slot_tot[r];
+                const Slot sl = w.slot[r];
+                rec.size = (int64_t)sl.size;
+                rec.sum_tot = (int64_t)sl.tot;
                 rec.first_toa = g.toa_min + skey[r];
-                const double sw = (double)w.slot_tot[r];
-                rec.cx = (float)((double)w.slot_wx[r] / sw);
-                rec.cy = (float)((double)w.slot_wy[r] / sw);
+                const double sw = (double)sl.tot;
+                rec.cx = (float)((double)sl.wx / sw);
+                rec.cy = (float)((double)sl.wy / sw);
                 g.out_rec[ord] = rec;
             }
             ++ord;
@@ -368,18 +375,18 @@ cudaError_t init_features_attributes() {
 }
 
 void launch_features(const Work &w, const Launch &L) {
-    k_accumulate<<<L.grid, ACC_THREADS, ACC_SMEM, L.stream>>>(w);
+    k_accumulate<<<L.fit(k_accumulate, ACC_THREADS, ACC_SMEM), ACC_THREADS, ACC_SMEM, L.stream>>>(w);
     L.mark("k_accumulate");
 }
 
 void launch_outputs(const Work &w, const Launch &L) {
-    k_labels<<<L.grid, 256, 0, L.stream>>>(w);
+    k_labels<<<L.fit(k_labels, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_labels");
     k_tile_scan<<<MAX_SEGS, 1024, 0, L.stream>>>(w);
     L.mark("k_tile_scan");
-    k_records<<<L.grid, TILE_WORDS, 0, L.stream>>>(w);
+    k_records<<<L.fit(k_records, TILE_WORDS, 0), TILE_WORDS, 0, L.stream>>>(w);
     L.mark("k_records");
-    k_stream_compact<<<L.grid, TILE_WORDS, 0, L.stream>>>(w);
+    k_stream_compact<<<L.fit(k_stream_compact, TILE_WORDS, 0), TILE_WORDS, 0, L.stream>>>(w);
     L.mark("k_stream_compact");
     k_stream_end<<<1, 256, 0, L.stream>>>(w);
     L.mark("k_stream_end");

@@ -316,16 +316,16 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
 // tile's hits on each pixel (16-bit compare-and-swap pushes).  Hit k walks the
 // lists of its 9 pixels; every earlier hit there within dt is an edge.
 //
-// Components without contended union-find: each hit points to the first
-// earlier neighbour it found (a forest, since parents have smaller ranks);
-// further neighbours go to an edge list.  Pointer jumping flattens the
-// forest, then each listed edge whose ends have different roots hooks the
-// larger root under the smaller (atomicMin); flatten and hook repeat until no
-// edge hooks (Shiloach-Vishkin style).  The surviving root of a component is
-// its smallest rank, i.e. its earliest hit.  A list longer than TAB_WALK (a
-// pile on one pixel) or more edges than the list holds send the tile to
-// k_tile_link instead.  Only the table entries a tile touched are reset
-// afterwards (Algorithm 3 step 7).
+// Components: each hit points to the smallest earlier neighbour it found (a
+// forest, since parents have smaller ranks, whose roots are the smallest
+// ranks of their trees); further neighbours go to an edge list.  After one
+// pointer-jumping pass over the forest, each listed edge is a lock-free union
+// that hooks the larger root under the smaller with compare-and-swap
+// (Jaiganesh & Burtscher's ECL-CC hooking), so the surviving root of a
+// component is its smallest rank, i.e. its earliest hit.  A list longer than
+// TAB_WALK (a pile on one pixel) or more edges than the list holds send the
+// tile to k_tile_link instead.  Only the table entries a tile touched are
+// reset afterwards (Algorithm 3 step 7).
 constexpr int TAB_THREADS = 1024;
 constexpr uint16_t TAB_NONE = 0xFFFFu;
 constexpr int TAB_WALK = 64;
@@ -333,10 +333,9 @@ constexpr int TAB_EDGES = 2 * TILE;
 
 struct TabShared {
     uint16_t tab[TAB_PIXELS];        // head of each pixel's list (rank), or TAB_NONE
-    uint32_t key[TILE];
-    uint32_t pix[TILE];
+    uint32_t key[TILE];              // per rank: key
+    uint16_t next[TILE];             // per rank: next rank on the same pixel
     uint32_t par[TILE];              // forest over ranks
-    uint16_t next[TILE];             // next rank on the same pixel
     uint32_t edges[TAB_EDGES];       // extra edges, k << 16 | j
     uint32_t nedges;
     uint32_t overflow;
@@ -371,6 +370,23 @@ __device__ __forceinline__ uint32_t tab_root(volatile uint32_t *par, uint32_t k)
     }
 }
 
+// Union of the components of a and b: hook the larger root under the
+// smaller.  A failed compare-and-swap means another thread hooked that root
+// first (each retry follows one completed hook, so there are fewer retries
+// than ranks); returns false only if that bound is exceeded.
+__device__ __forceinline__ bool tab_union(volatile uint32_t *par, uint32_t a, uint32_t b) {
+    uint32_t ra = tab_root(par, a), rb = tab_root(par, b);
+    for (int it = 0; it < TILE; ++it) {
+        if (ra == rb) return true;
+        if (ra > rb) { const uint32_t t = ra; ra = rb; rb = t; }
+        const uint32_t old = atomicCAS(const_cast<uint32_t *>(par) + rb, rb, ra);
+        if (old == rb) return true;
+        rb = tab_root(par, old);
+        ra = tab_root(par, ra);
+    }
+    return false;
+}
+
 __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     extern __shared__ __align__(16) unsigned char tab_raw[];
     TabShared &S = *reinterpret_cast<TabShared *>(tab_raw);
@@ -402,7 +418,6 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             const uint32_t k = q * TAB_THREADS + threadIdx.x;
             if (k < n_t) {
                 S.key[k] = kv[q];
-                S.pix[k] = pv[q];
                 S.next[k] = tab_push(S.tab, tab_pid(pv[q], W), (uint16_t)k);
             }
         }
@@ -432,8 +447,11 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                             uint32_t other = j;
                             if (parent == k) { parent = j; continue; }
                             if (j < parent) { other = parent; parent = j; }
-                            if (nc < CAND) {
-                                cand[nc++] = other;
+                            if (nc < CAND) {   // constant indices keep cand in registers
+#pragma unroll
+                                for (int i = 0; i < CAND; ++i)
+                                    if (i == nc) cand[i] = other;
+                                ++nc;
                             } else {   // rare: straight to the edge list
                                 const uint32_t slot = atomicAdd(&S.nedges, 1u);
                                 if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | other;
@@ -445,8 +463,10 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 S.par[k] = parent;
             }
             const uint32_t most = __reduce_max_sync(0xffffffffu, (uint32_t)nc);
-            for (uint32_t c = 0; c < most; ++c) {
-                const bool has = (int)c < nc;
+#pragma unroll
+            for (int c = 0; c < CAND; ++c) {
+                if (c >= (int)most) break;
+                const bool has = c < nc;
                 const uint32_t m = __ballot_sync(0xffffffffu, has);
                 uint32_t slot0 = 0;
                 if (lane == 0) slot0 = atomicAdd(&S.nedges, (uint32_t)__popc(m));
@@ -456,7 +476,24 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             }
         }
         __syncthreads();
-        if (S.overflow || S.nedges > TAB_EDGES) {   // leave this tile to k_tile_link
+        bool redo = S.overflow || S.nedges > TAB_EDGES;
+        if (!redo) {
+            const uint32_t ne = S.nedges;
+            // flatten the forest, then one union per extra edge
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                if (k < n_t) vpar[k] = tab_root(vpar, k);
+            }
+            __syncthreads();
+            bool ok = true;
+            for (uint32_t e = threadIdx.x; e < ne; e += TAB_THREADS) {
+                const uint32_t ed = S.edges[e];
+                ok &= tab_union(vpar, ed >> 16, ed & 0xFFFFu);
+            }
+            redo = !__syncthreads_and(ok);
+        }
+        if (redo) {   // leave this tile to k_tile_link
             if (threadIdx.x == 0) {
                 const uint32_t slot = atomicAdd(&w.prob->redo_count, 1u);
                 w.redo[slot] = t;
@@ -469,31 +506,11 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             __syncthreads();
             continue;
         }
-        const uint32_t ne = S.nedges;
-        while (true) {
-            // flatten: every rank jumps to its root (parents only move rootwards)
-#pragma unroll
-            for (int q = 0; q < ITEMS; ++q) {
-                const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                if (k < n_t) vpar[k] = tab_root(vpar, k);
-            }
-            __syncthreads();
-            bool hooked = false;
-            for (uint32_t e = threadIdx.x; e < ne; e += TAB_THREADS) {   // hook
-                const uint32_t ed = S.edges[e];
-                const uint32_t ra = vpar[ed >> 16], rb = vpar[ed & 0xFFFFu];
-                if (ra != rb) {
-                    atomicMin(&S.par[ra > rb ? ra : rb], ra < rb ? ra : rb);
-                    hooked = true;
-                }
-            }
-            if (!__syncthreads_or(hooked)) break;
-        }
 #pragma unroll
         for (int q = 0; q < ITEMS; ++q) {
             const uint32_t k = q * TAB_THREADS + threadIdx.x;
             if (k < n_t) {
-                const uint32_t r = vpar[k];
+                const uint32_t r = tab_root(vpar, k);
                 w.parent[begin + k] = begin + r;
                 if (r == k) init_slot(w, begin + k);
                 S.tab[tab_pid(pv[q], W)] = TAB_NONE;   // reset only what this tile touched
@@ -607,14 +624,7 @@ __global__ void __launch_bounds__(256) k_flatten(Work w) {
             // other threads' path halving with a stale ancestor)
             sroot[s] = r;
             w.root_of[pos[q]] = r;
-            if (r == s) {
-                w.slot_size[r] = 0;
-                w.slot_min[r] = 0xFFFFFFFFu;
-                w.slot_maxkey[r] = 0;
-                w.slot_tot[r] = 0;
-                w.slot_wx[r] = 0;
-                w.slot_wy[r] = 0;
-            }
+            if (r == s) init_slot(w, r);
         }
     }
 }
@@ -635,16 +645,16 @@ cudaError_t init_kernel_attributes() {
 
 void launch_tile_border(const Work &w, const Launch &L) {
     const int smem = TILE_LINK_SMEM;
-    k_tile_link_table<<<L.sms > 0 ? L.sms : L.grid, TAB_THREADS, TAB_SMEM, L.stream>>>(w);
+    k_tile_link_table<<<L.fit(k_tile_link_table, TAB_THREADS, TAB_SMEM), TAB_THREADS, TAB_SMEM, L.stream>>>(w);
     L.mark("k_tile_link_table");
-    k_tile_link<<<L.grid, LINK_THREADS, smem, L.stream>>>(w);
+    k_tile_link<<<L.fit(k_tile_link, LINK_THREADS, smem), LINK_THREADS, smem, L.stream>>>(w);
     L.mark("k_tile_link");
-    k_border_link<<<L.grid, BORDER_THREADS, 0, L.stream>>>(w);
+    k_border_link<<<L.fit(k_border_link, BORDER_THREADS, 0), BORDER_THREADS, 0, L.stream>>>(w);
     L.mark("k_border_link");
 }
 
 void launch_flatten(const Work &w, const Launch &L) {
-    k_flatten<<<L.grid, 256, 0, L.stream>>>(w);
+    k_flatten<<<L.fit(k_flatten, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_flatten");
 }
 

@@ -33,7 +33,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // byte offsets of every work array inside the scratch array
 struct Layout {
     size_t seg, prob, tile_seg, redo, keys0, keys1, vals0, vals1, spix, stot, parent, root_of,
-        slot_size, slot_min, slot_maxkey, slot_tot, slot_wx, slot_wy, flag_label, flag_closed,
+        slot, flag_label, flag_closed,
         tile_cnt, tile_base, hist, segtot, total;
 };
 
@@ -52,12 +52,7 @@ constexpr Layout make_layout() {
     l.stot = o; o += align256(NA_POS * 2);
     l.parent = o; o += align256(NA_POS * 4);
     l.root_of = o; o += align256(NA_POS * 4);
-    l.slot_size = o; o += align256(NA_POS * 4);
-    l.slot_min = o; o += align256(NA_POS * 4);
-    l.slot_maxkey = o; o += align256(NA_POS * 4);
-    l.slot_tot = o; o += align256(NA_POS * 8);
-    l.slot_wx = o; o += align256(NA_POS * 8);
-    l.slot_wy = o; o += align256(NA_POS * 8);
+    l.slot = o; o += align256(NA_POS * sizeof(Slot));
     l.flag_label = o; o += align256((NA_POS / 32 + 1) * 4);
     l.flag_closed = o; o += align256((NA_POS / 32 + 1) * 4);
     l.tile_cnt = o; o += align256(2 * NA_TILES * 4);
@@ -153,12 +148,7 @@ extern "C" int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width,
     w.stot = reinterpret_cast<uint16_t *>(base + NA.stot);
     w.parent = reinterpret_cast<uint32_t *>(base + NA.parent);
     w.root_of = reinterpret_cast<uint32_t *>(base + NA.root_of);
-    w.slot_size = reinterpret_cast<uint32_t *>(base + NA.slot_size);
-    w.slot_min = reinterpret_cast<uint32_t *>(base + NA.slot_min);
-    w.slot_maxkey = reinterpret_cast<uint32_t *>(base + NA.slot_maxkey);
-    w.slot_tot = reinterpret_cast<unsigned long long *>(base + NA.slot_tot);
-    w.slot_wx = reinterpret_cast<unsigned long long *>(base + NA.slot_wx);
-    w.slot_wy = reinterpret_cast<unsigned long long *>(base + NA.slot_wy);
+    w.slot = reinterpret_cast<Slot *>(base + NA.slot);
     w.lab_tmp = nullptr;   // streaming only
     w.flag_label = reinterpret_cast<uint32_t *>(base + NA.flag_label);
     w.flag_closed = reinterpret_cast<uint32_t *>(base + NA.flag_closed);

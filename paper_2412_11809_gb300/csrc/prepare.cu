@@ -248,7 +248,7 @@ void launch_setup(const Work &w, int nsegs, const Launch &L) {
     L.mark("k_setup");
 }
 void launch_prepare(const Work &w, const Launch &L) {
-    k_prepare<<<L.grid, 256, 0, L.stream>>>(w);
+    k_prepare<<<L.fit(k_prepare, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_prepare");
 }
 void launch_seg_finalize(const Work &w, const Launch &L) {
@@ -256,11 +256,11 @@ void launch_seg_finalize(const Work &w, const Launch &L) {
     L.mark("k_seg_finalize");
 }
 void launch_make_keys(const Work &w, const Launch &L) {
-    k_make_keys<<<L.grid, 256, 0, L.stream>>>(w);
+    k_make_keys<<<L.fit(k_make_keys, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_make_keys");
 }
 void launch_gather(const Work &w, const Launch &L) {
-    k_gather<<<L.grid, 256, 0, L.stream>>>(w);
+    k_gather<<<L.fit(k_gather, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_gather");
 }
 

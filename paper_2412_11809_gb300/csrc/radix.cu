@@ -208,11 +208,11 @@ void launch_radix_pass(const Work &w, int pass, const Launch &L) {
     static const char *sc[4] = {"k_radix_scan0", "k_radix_scan1", "k_radix_scan2", "k_radix_scan3"};
     static const char *dn[4] = {"k_radix_downsweep0", "k_radix_downsweep1", "k_radix_downsweep2",
                                 "k_radix_downsweep3"};
-    k_radix_upsweep<<<L.grid, 256, 0, L.stream>>>(w, pass);
+    k_radix_upsweep<<<L.fit(k_radix_upsweep, 256, 0), 256, 0, L.stream>>>(w, pass);
     L.mark(up[pass & 3]);
     k_radix_scan<<<RADIX, 1024, 0, L.stream>>>(w, pass);
     L.mark(sc[pass & 3]);
-    k_radix_downsweep<<<L.grid, DS_THREADS, 0, L.stream>>>(w, pass);
+    k_radix_downsweep<<<L.fit(k_radix_downsweep, DS_THREADS, 0), DS_THREADS, 0, L.stream>>>(w, pass);
     L.mark(dn[pass & 3]);
 }
 

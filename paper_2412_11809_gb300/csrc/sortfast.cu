@@ -192,6 +192,8 @@ struct LmShared {
     uint32_t pos[TILE];
     uint32_t pix[TILE];
     uint16_t tot[TILE];
+    uint16_t rank[TILE];         // output rank of each moving element
+    uint32_t cut[2];
 };
 constexpr int LM_SMEM = (int)sizeof(LmShared);
 
@@ -203,18 +205,19 @@ __device__ __forceinline__ bool lm_below(uint32_t ka, uint32_t pa, uint32_t kb, 
 // Only the part of the window where the two halves interleave moves: A's
 // elements above B's first and B's elements below A's last.  Keys and
 // positions of a band of MERGE_BAND entries on each side of the border are
-// read first to locate that overlap (the whole window when the overlap
-// reaches the band's edge); pixels and ToTs are read, and everything
-// written back, for the overlap only.  Each moving element's output rank =
-// its index in its own part + the number of the other part's elements that
-// sort before it (binary search; the lanes of a warp search for
-// neighbouring values, so their probes mostly coincide).
+// read first, and the two cut points counted (A sorted, so the number of its
+// elements below B's first is where B's first goes); the whole window is
+// taken when the overlap reaches the band's edge.  Each moving element's
+// output rank = its index in its own part + the number of the other part's
+// elements that sort before it (binary search; the lanes of a warp search
+// for neighbouring values, so their probes mostly coincide).  The moving
+// elements' pixels and ToTs are staged in shared memory, so that the final
+// pass can write every array straight to its output position.
 constexpr uint32_t MERGE_BAND = TILE / 4;
 
 __global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
     extern __shared__ __align__(16) unsigned char lm_raw[];
     LmShared &S = *reinterpret_cast<LmShared *>(lm_raw);
-    __shared__ uint32_t s_cut[2];
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
@@ -230,74 +233,60 @@ __global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
         for (uint32_t band = MERGE_BAND;; band = TILE / 2) {
             const uint32_t na = band, nb = band < nb_all ? band : nb_all;
             const uint32_t a0 = begin - na;   // A = [a0, begin), B = [begin, begin + nb)
+            if (threadIdx.x < 2) S.cut[threadIdx.x] = 0;
             for (uint32_t j = threadIdx.x; j < na + nb; j += LS_THREADS) {
                 S.key[j] = w.keys[0][a0 + j];
                 S.pos[j] = w.vals[0][a0 + j];
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                // ia = A elements below B[0]; ib = B elements below A[last]
-                uint32_t lo = 0, hi = na;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (lm_below(S.key[mid], S.pos[mid], S.key[na], S.pos[na])) lo = mid + 1; else hi = mid;
+            {   // ia = A elements below B[0]; ib = B elements below A[last]
+                const uint32_t kb0 = S.key[na], pb0 = S.pos[na], kal = S.key[na - 1], pal = S.pos[na - 1];
+                uint32_t ca = 0, cb = 0;
+                for (uint32_t j = threadIdx.x; j < na; j += LS_THREADS)
+                    ca += lm_below(S.key[j], S.pos[j], kb0, pb0);
+                for (uint32_t j = threadIdx.x; j < nb; j += LS_THREADS)
+                    cb += lm_below(S.key[na + j], S.pos[na + j], kal, pal);
+                for (int o = 16; o; o >>= 1) {
+                    ca += __shfl_xor_sync(0xffffffffu, ca, o);
+                    cb += __shfl_xor_sync(0xffffffffu, cb, o);
                 }
-                s_cut[0] = lo;
-                lo = na; hi = na + nb;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (lm_below(S.key[mid], S.pos[mid], S.key[na - 1], S.pos[na - 1])) lo = mid + 1; else hi = mid;
+                if ((threadIdx.x & 31) == 0) {
+                    if (ca) atomicAdd(&S.cut[0], ca);
+                    if (cb) atomicAdd(&S.cut[1], cb);
                 }
-                s_cut[1] = lo - na;
             }
             __syncthreads();
-            const uint32_t ia = s_cut[0], ib = s_cut[1];
+            const uint32_t ia = S.cut[0], ib = S.cut[1];
             const bool contained = (ia > 0 || na == TILE / 2) && (ib < nb || nb == nb_all);
             if (!contained && band != TILE / 2) {
                 __syncthreads();
                 continue;   // overlap wider than the band: take the whole window
             }
-            // moving part: A[ia, na) and B[0, ib), output positions a0 + ia ...
+            // moving part: A[ia, na) then B[0, ib) (indices in S); outputs a0 + ia ...
             const uint32_t ma = na - ia, m = ma + ib;
-            uint32_t rk[LS_ITEMS], rp[LS_ITEMS], rx[LS_ITEMS], out[LS_ITEMS];
-            uint16_t rt[LS_ITEMS];
-#pragma unroll
-            for (int r = 0; r < LS_ITEMS; ++r) {
-                const uint32_t j = r * LS_THREADS + threadIdx.x;
-                if (j < m) {
-                    const uint32_t src = j < ma ? ia + j : na + (j - ma);   // index in S
-                    rk[r] = S.key[src];
-                    rp[r] = S.pos[src];
-                    rx[r] = w.spix[a0 + src];
-                    rt[r] = w.stot[a0 + src];
-                    const bool in_a = j < ma;
-                    uint32_t lo = in_a ? na : ia, hi = in_a ? na + ib : na;   // the other part
-                    const uint32_t first = lo;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (lm_below(S.key[mid], S.pos[mid], rk[r], rp[r])) lo = mid + 1; else hi = mid;
-                    }
-                    out[r] = (in_a ? j : j - ma) + (lo - first);
+            for (uint32_t j = threadIdx.x; j < m; j += LS_THREADS) {
+                const bool in_a = j < ma;
+                const uint32_t src = in_a ? ia + j : na + (j - ma);
+                const uint32_t kk = S.key[src], pp = S.pos[src];
+                uint32_t lo = in_a ? na : ia, hi = in_a ? na + ib : na;   // the other part
+                const uint32_t first = lo;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (lm_below(S.key[mid], S.pos[mid], kk, pp)) lo = mid + 1; else hi = mid;
                 }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < LS_ITEMS; ++r) {
-                const uint32_t j = r * LS_THREADS + threadIdx.x;
-                if (j < m) {
-                    S.key[out[r]] = rk[r];
-                    S.pos[out[r]] = rp[r];
-                    S.pix[out[r]] = rx[r];
-                    S.tot[out[r]] = rt[r];
-                }
+                S.rank[j] = (uint16_t)((in_a ? j : j - ma) + (lo - first));
+                S.pix[src] = w.spix[a0 + src];
+                S.tot[src] = w.stot[a0 + src];
             }
             __syncthreads();
             const uint32_t o0 = a0 + ia;
             for (uint32_t j = threadIdx.x; j < m; j += LS_THREADS) {
-                w.keys[0][o0 + j] = S.key[j];
-                w.vals[0][o0 + j] = S.pos[j];
-                w.spix[o0 + j] = S.pix[j];
-                w.stot[o0 + j] = S.tot[j];
+                const uint32_t src = j < ma ? ia + j : na + (j - ma);
+                const uint32_t o = o0 + S.rank[j];
+                w.keys[0][o] = S.key[src];
+                w.vals[0][o] = S.pos[src];
+                w.spix[o] = S.pix[src];
+                w.stot[o] = S.tot[src];
             }
             __syncthreads();
             break;
@@ -333,11 +322,11 @@ cudaError_t init_sortfast_attributes() {
 }
 
 void launch_sort_fast(const Work &w, const Launch &L) {
-    k_tile_sort<<<L.grid, LS_THREADS, LS_SMEM, L.stream>>>(w);
+    k_tile_sort<<<L.fit(k_tile_sort, LS_THREADS, LS_SMEM), LS_THREADS, LS_SMEM, L.stream>>>(w);
     L.mark("k_tile_sort");
-    k_tile_merge<<<L.grid, LS_THREADS, LM_SMEM, L.stream>>>(w);
+    k_tile_merge<<<L.fit(k_tile_merge, LS_THREADS, LM_SMEM), LS_THREADS, LM_SMEM, L.stream>>>(w);
     L.mark("k_tile_merge");
-    k_sort_check<<<L.grid, 256, 0, L.stream>>>(w);
+    k_sort_check<<<L.fit(k_sort_check, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_sort_check");
 }
 

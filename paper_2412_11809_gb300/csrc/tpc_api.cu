@@ -24,6 +24,20 @@ namespace {
 
 constexpr int SEG_RING = 8;
 
+// occupancy(): cudaOccupancyMaxActiveBlocksPerMultiprocessor, remembered per
+// (device, kernel, block size, shared memory) so that launches and graph
+// captures do not repeat the query.
+struct OccEntry {
+    int dev;
+    const void *kernel;
+    int threads;
+    size_t smem;
+    int blocks;
+};
+std::mutex occ_mu;
+std::vector<OccEntry> occ_cache;
+
+
 struct DevMem {
     std::vector<void *> ptrs;
     size_t bytes = 0;
@@ -54,7 +68,8 @@ struct Workspace {
 
     static size_t bytes_for(size_t pos_cap) {
         const size_t tiles = pos_cap / TILE + MAX_SEGS;
-        return pos_cap * (4 * 4 + 4 * 4 + 3 * 8 + 8 + 2 * 0) + pos_cap / 4 +
+        // keys, vals (2 each), spix, parent, root_of: 4 B; stot: 2 B; slot; lab_tmp: 8 B
+        return pos_cap * (7 * 4 + 2 + sizeof(Slot) + 8) + pos_cap / 4 +
                tiles * (4 + 4 * 4 + RADIX * 4) + MAX_SEGS * (RADIX * 4 + sizeof(Seg)) + (1 << 16);
     }
 
@@ -81,12 +96,7 @@ struct Workspace {
         w.stot = mem.alloc<uint16_t>(P, e);
         w.parent = mem.alloc<uint32_t>(P, e);
         w.root_of = mem.alloc<uint32_t>(P, e);
-        w.slot_size = mem.alloc<uint32_t>(P, e);
-        w.slot_min = mem.alloc<uint32_t>(P, e);
-        w.slot_maxkey = mem.alloc<uint32_t>(P, e);
-        w.slot_tot = mem.alloc<unsigned long long>(P, e);
-        w.slot_wx = mem.alloc<unsigned long long>(P, e);
-        w.slot_wy = mem.alloc<unsigned long long>(P, e);
+        w.slot = mem.alloc<Slot>(P, e);
         w.lab_tmp = mem.alloc<uint64_t>(P, e);
         w.flag_label = mem.alloc<uint32_t>(P / 32 + 1, e);
         w.flag_closed = mem.alloc<uint32_t>(P / 32 + 1, e);
@@ -232,6 +242,19 @@ struct tpc_ctx {
     }
 };
 
+int tpc::occupancy(const void *kernel, int threads, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(occ_mu);
+    for (const OccEntry &e : occ_cache)
+        if (e.dev == dev && e.kernel == kernel && e.threads == threads && e.smem == smem) return e.blocks;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem) != cudaSuccess || blocks < 1)
+        blocks = 1;
+    occ_cache.push_back({dev, kernel, threads, smem, blocks});
+    return blocks;
+}
+
 namespace {
 
 int grid_of(const tpc_ctx *c) {
@@ -288,10 +311,10 @@ void enqueue_kernels(const Work &w, int nsegs, const Launch &L) {
 // Run the fixed kernel sequence, from a CUDA graph captured on first use
 // (and re-captured when the workspace or the segment count changes).
 cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, Tracer *tr = nullptr) {
-    const Launch L{grid_of(owner), st, nullptr, owner->sms};
+    const Launch L{grid_of(owner), st, nullptr, owner->sms, owner->ctas_per_sm};
     if (tr) {   // kernels one by one with an event after each (no graph)
         cudaEventRecord(tr->ev[0], st);
-        enqueue_kernels(ws.w, nsegs, Launch{L.grid, st, tr, owner->sms});
+        enqueue_kernels(ws.w, nsegs, Launch{L.grid, st, tr, owner->sms, L.cap});
         return cudaGetLastError();
     }
     if (!owner->graph || owner->graph_nsegs != nsegs || owner->graph_pos_cap != ws.pos_cap ||
@@ -306,7 +329,7 @@ cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, 
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            enqueue_kernels(ws.w, nsegs, Launch{L.grid, cap_st, nullptr, owner->sms});
+            enqueue_kernels(ws.w, nsegs, Launch{L.grid, cap_st, nullptr, owner->sms, L.cap});
             e = cudaStreamEndCapture(cap_st, &g);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&owner->graph, g, 0);
@@ -613,7 +636,7 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
     if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
     const Work &w = c->ws.w;
     const VarWork &v = c->vs.v;
-    const Launch L{grid_of(c), c->stream, tr, c->sms};
+    const Launch L{grid_of(c), c->stream, tr, c->sms, c->ctas_per_sm};
     if (tr) cudaEventRecord(tr->ev[0], c->stream);
     launch_setup(w, 1, L);
     launch_prepare(w, L);

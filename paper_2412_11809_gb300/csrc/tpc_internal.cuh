@@ -98,6 +98,18 @@ struct Prob {
     uint32_t pad;
 };
 
+// Feature sums of one cluster, kept at its root's sorted position.  One
+// 40-byte record (8-byte aligned, so exactly two 32-byte sectors) instead of
+// six arrays: the scattered per-root accesses touch 2 sectors, not 6.
+struct Slot {
+    unsigned long long tot, wx, wy;   // sum ToT, sum ToT*x, sum ToT*y
+    uint32_t size;
+    uint32_t min;                     // smallest position
+    uint32_t maxkey;                  // largest key (last ToA - toa_min)
+    uint32_t pad;
+};
+static_assert(sizeof(Slot) == 40, "slot layout");
+
 // Work arrays (device), sized for pos_cap positions and tile_cap tiles.
 struct Work {
     Seg *seg;
@@ -110,10 +122,7 @@ struct Work {
     uint16_t *stot;            // sorted positions: ToT
     uint32_t *parent;          // union-find over sorted positions
     uint32_t *root_of;         // per position: root (a sorted position)
-    uint32_t *slot_size;       // per root
-    uint32_t *slot_min;        // per root: smallest position
-    uint32_t *slot_maxkey;     // per root: largest key (last ToA - toa_min)
-    unsigned long long *slot_tot, *slot_wx, *slot_wy;
+    Slot *slot;                // per root: its cluster's features
     uint64_t *lab_tmp;         // streaming: label per position
     uint32_t *flag_label;      // bit per position: label hit of a finalised cluster
     uint32_t *flag_closed;     // bit per position: hit of a finalised cluster
@@ -152,12 +161,12 @@ __device__ __forceinline__ uint32_t sorted_sel(const Prob &p) { return p.npasses
 
 // Zero the feature slot of root r (a tile root; every global root is one).
 __device__ __forceinline__ void init_slot(const Work &w, uint32_t r) {
-    w.slot_size[r] = 0;
-    w.slot_min[r] = 0xFFFFFFFFu;
-    w.slot_maxkey[r] = 0;
-    w.slot_tot[r] = 0;
-    w.slot_wx[r] = 0;
-    w.slot_wy[r] = 0;
+    unsigned long long *q = reinterpret_cast<unsigned long long *>(w.slot + r);
+    q[0] = 0;
+    q[1] = 0;
+    q[2] = 0;
+    q[3] = 0xFFFFFFFF00000000ull;   // size = 0, min = all ones
+    q[4] = 0;                       // maxkey = 0
 }
 
 // Union-find on global memory over sorted positions.  Roots are the smaller
@@ -235,12 +244,28 @@ struct Tracer {
     }
 };
 
+// CTAs of `kernel` one SM holds at once with this block size and dynamic
+// shared memory (registers included); cached per device.
+int occupancy(const void *kernel, int threads, size_t smem);
+
 struct Launch {
-    int grid;          // persistent CTAs
+    int grid;          // fallback grid when the SM count is unknown
     cudaStream_t stream;
     Tracer *tr = nullptr;
-    int sms = 0;       // SM count (one CTA per SM for the shared-memory-heavy kernels)
+    int sms = 0;       // SM count
+    int cap = 0;       // at most this many CTAs per SM (0 = as many as fit)
     void mark(const char *name) const { if (tr) tr->mark(name, stream); }
+    // Grid of a persistent kernel (a strided loop over tiles): exactly one
+    // wave, every SM filled to the kernel's occupancy.  A grid that is not a
+    // whole multiple of the resident CTAs would leave a partial second wave
+    // running on a fraction of each SM.
+    template <class K>
+    int fit(K *kernel, int threads, size_t smem) const {
+        if (sms <= 0) return grid;
+        int per_sm = occupancy(reinterpret_cast<const void *>(kernel), threads, smem);
+        if (cap > 0 && per_sm > cap) per_sm = cap;
+        return sms * (per_sm > 0 ? per_sm : 1);
+    }
 };
 
 cudaError_t init_kernel_attributes();   // once per process and device, before capture

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_global_round(Work w, VarWork v) {
 }
 
 void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const Launch &L) {
-    k_var_keys<<<L.grid, 256, 0, L.stream>>>(w, v, by_pixel);
+    k_var_keys<<<L.fit(k_var_keys, 256, 0), 256, 0, L.stream>>>(w, v, by_pixel);
     L.mark(by_pixel ? "k_var_keys_pixel" : "k_var_keys_root");
 }
 
@@ -219,22 +219,22 @@ Work variant_view(const Work &w, const VarWork &v) {
 }
 
 void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L) {
-    k_static_sweep<<<L.grid, 128, 0, L.stream>>>(w, v);
+    k_static_sweep<<<L.fit(k_static_sweep, 128, 0), 128, 0, L.stream>>>(w, v);
     L.mark("k_static_sweep");
 }
 
 void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, const Launch &L) {
     cudaMemsetAsync(v.pix_start, 0, (npixels + 1) * sizeof(uint32_t), L.stream);
-    k_pixel_hist<<<L.grid, 256, 0, L.stream>>>(w, v);
+    k_pixel_hist<<<L.fit(k_pixel_hist, 256, 0), 256, 0, L.stream>>>(w, v);
     k_pixel_scan<<<1, 1024, 0, L.stream>>>(w, v);
     L.mark("k_pixel_hist_scan");
 }
 
 void launch_global_round(const Work &w, const VarWork &v, const Launch &L) {
     cudaMemsetAsync(v.changed, 0, sizeof(uint32_t), L.stream);
-    k_group_last_reset<<<L.grid, 256, 0, L.stream>>>(w, v);
-    k_group_last<<<L.grid, 256, 0, L.stream>>>(w, v);
-    k_global_round<<<L.grid, 256, 0, L.stream>>>(w, v);
+    k_group_last_reset<<<L.fit(k_group_last_reset, 256, 0), 256, 0, L.stream>>>(w, v);
+    k_group_last<<<L.fit(k_group_last, 256, 0), 256, 0, L.stream>>>(w, v);
+    k_global_round<<<L.fit(k_global_round, 256, 0), 256, 0, L.stream>>>(w, v);
     L.mark("k_global_round");
 }
 
