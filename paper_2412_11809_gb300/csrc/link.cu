@@ -33,7 +33,13 @@
 namespace tpc {
 
 constexpr int LINK_THREADS = 512;
-constexpr uint32_t TAB_PIXELS = 1u << 16;      // table mode up to this many pixels
+constexpr uint32_t TAB_CAP = 68u << 10;        // table entries: sensor plus a 1-pixel frame
+
+// Table mode: the sensor with a frame of empty pixels around it fits the
+// shared-memory table (a 256 x 256 sensor takes 258 x 258 entries).
+__device__ __forceinline__ bool table_mode(uint32_t W, uint32_t H) {
+    return (uint64_t)(W + 2) * (H + 2) <= TAB_CAP;
+}
 constexpr int NBUCKETS = 2048;                // hashed 4x4-pixel cells
 constexpr int HALO_BATCH = 2048;
 constexpr int BORDER_THREADS = 256;
@@ -248,7 +254,7 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         const uint32_t n_t = end - begin, W = g.width, H = g.height, dt = g.dt;
-        if (u < n_large && W * H <= TAB_PIXELS) continue;   // done by k_tile_link_table
+        if (u < n_large && table_mode(W, H)) continue;   // done by k_tile_link_table
         const uint32_t cw = (W + 3) >> 2;
         {
             constexpr int ITEMS = TILE / LINK_THREADS;
@@ -310,11 +316,13 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
 }
 
 // ---------------------------------------------------------------------------
-// Table mode, for sensors of at most TAB_PIXELS pixels: a direct-mapped
+// Table mode, for sensors that fit TAB_CAP with a frame: a direct-mapped
 // per-pixel table in shared memory (the paper's per-pixel matrix with 2-byte
 // entries, Algorithm 3 step 4 and Section 4.2) heads a lock-free list of the
 // tile's hits on each pixel (16-bit compare-and-swap pushes).  Hit k walks the
-// lists of its 9 pixels; every earlier hit there within dt is an edge.
+// lists of its 9 pixels; every earlier hit there within dt is an edge.  The
+// table has a frame of never-used entries around the sensor, so the 9
+// lookups need no bounds checks.
 //
 // Components: each hit points to the smallest earlier neighbour it found (a
 // forest, since parents have smaller ranks, whose roots are the smallest
@@ -332,7 +340,7 @@ constexpr int TAB_WALK = 64;
 constexpr int TAB_EDGES = 2 * TILE;
 
 struct TabShared {
-    uint16_t tab[TAB_PIXELS];        // head of each pixel's list (rank), or TAB_NONE
+    uint16_t tab[TAB_CAP];           // head of each pixel's list (rank), or TAB_NONE
     uint32_t key[TILE];              // per rank: key
     uint16_t next[TILE];             // per rank: next rank on the same pixel
     uint32_t par[TILE];              // forest over ranks
@@ -342,8 +350,9 @@ struct TabShared {
 };
 constexpr int TAB_SMEM = (int)sizeof(TabShared);
 
+// table entry of pixel (x, y): row y + 1, column x + 1 of a (W + 2)-wide table
 __device__ __forceinline__ uint32_t tab_pid(uint32_t pix, uint32_t W) {
-    return (pix >> 16) * W + (pix & 0xFFFFu);
+    return ((pix >> 16) + 1) * (W + 2) + (pix & 0xFFFFu) + 1;
 }
 
 // push rank k on pixel pid's list; returns the previous head
@@ -359,14 +368,16 @@ __device__ __forceinline__ uint16_t tab_push(uint16_t *tab, uint32_t pid, uint16
     }
 }
 
-// root of k by pointer jumping (parents only ever move towards the root)
-__device__ __forceinline__ uint32_t tab_root(volatile uint32_t *par, uint32_t k) {
-    uint32_t p = par[k];
+// root of x with path halving: every other node on the way is pointed at its
+// grandparent (parents only ever move towards the root, so this is safe
+// against concurrent hooks, which only ever rewrite roots)
+__device__ __forceinline__ uint32_t tab_root(volatile uint32_t *par, uint32_t x) {
     while (true) {
-        const uint32_t q = par[p];
-        if (q == p) return p;
-        par[k] = q;
-        p = q;
+        const uint32_t p = par[x];
+        const uint32_t gp = par[p];
+        if (p == gp) return p;
+        par[x] = gp;
+        x = gp;
     }
 }
 
@@ -395,13 +406,13 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
     const int lane = threadIdx.x & 31;
-    for (uint32_t i = threadIdx.x; i < TAB_PIXELS / 2; i += TAB_THREADS)
+    for (uint32_t i = threadIdx.x; i < TAB_CAP / 2; i += TAB_THREADS)
         reinterpret_cast<uint32_t *>(S.tab)[i] = 0xFFFFFFFFu;
     __syncthreads();
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         const uint32_t W = g.width, H = g.height, dt = g.dt;
-        if (W * H > TAB_PIXELS) continue;   // k_tile_link handles larger sensors
+        if (!table_mode(W, H)) continue;   // k_tile_link handles larger sensors
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         const uint32_t n_t = end - begin;
@@ -433,32 +444,46 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             int nc = 0;
             if (k < n_t) {
                 const uint32_t key = kv[q];
-                const int x = (int)(pv[q] & 0xFFFFu), y = (int)(pv[q] >> 16);
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int ny = y + dy;
-                    if (ny < 0 || ny >= (int)H) continue;
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int nx = x + dx;
-                        if (nx < 0 || nx >= (int)W) continue;
-                        uint32_t j = S.tab[(uint32_t)ny * W + (uint32_t)nx];
-                        int steps = 0;
-                        for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps) {
-                            if (j >= k || key - S.key[j] > dt) continue;
-                            uint32_t other = j;
-                            if (parent == k) { parent = j; continue; }
-                            if (j < parent) { other = parent; parent = j; }
-                            if (nc < CAND) {   // constant indices keep cand in registers
+                const uint32_t W2 = W + 2, centre = tab_pid(pv[q], W);
+                // j: an earlier neighbour within dt
+                auto consider = [&](uint32_t j) {
+                    uint32_t other = j;
+                    if (parent == k) { parent = j; return; }
+                    if (j < parent) { other = parent; parent = j; }
+                    if (nc < CAND) {
 #pragma unroll
-                                for (int i = 0; i < CAND; ++i)
-                                    if (i == nc) cand[i] = other;
-                                ++nc;
-                            } else {   // rare: straight to the edge list
-                                const uint32_t slot = atomicAdd(&S.nedges, 1u);
-                                if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | other;
-                            }
-                        }
-                        if (j != TAB_NONE) S.overflow = 1;
+                        for (int i = 0; i < CAND; ++i)
+                            if (i == nc) cand[i] = other;
+                        ++nc;
+                    } else {
+                        const uint32_t slot = atomicAdd(&S.nedges, 1u);
+                        if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | other;
                     }
+                };
+                // heads of the 9 lists first (independent loads), then the head
+                // entries without loops; lists with a second entry (a pixel hit
+                // more than once in the tile: rare) are walked afterwards
+                uint32_t hd[9];
+#pragma unroll
+                for (int n = 0; n < 9; ++n) hd[n] = S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)];
+                uint32_t more = 0;
+#pragma unroll
+                for (int n = 0; n < 9; ++n) {
+                    const uint32_t j = hd[n];
+                    if (j != TAB_NONE) {
+                        const uint32_t kj = S.key[j];
+                        more |= (S.next[j] != TAB_NONE ? 1u : 0u) << n;
+                        if (j < k && key - kj <= dt) consider(j);
+                    }
+                }
+                while (more) {   // lists holding more than one hit
+                    const int n = __ffs(more) - 1;
+                    more &= more - 1;
+                    uint32_t j = S.next[S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)]];
+                    int steps = 1;
+                    for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps)
+                        if (j < k && key - S.key[j] <= dt) consider(j);
+                    if (j != TAB_NONE) S.overflow = 1;
                 }
                 S.par[k] = parent;
             }
@@ -487,8 +512,14 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             }
             __syncthreads();
             bool ok = true;
-            for (uint32_t e = threadIdx.x; e < ne; e += TAB_THREADS) {
-                const uint32_t ed = S.edges[e];
+            // edges are listed warp by warp, so neighbouring entries tend to
+            // share roots: lanes take entries ne / 32 apart (fewer colliding
+            // compare-and-swaps within a warp)
+            const uint32_t ccol = (ne + 31) >> 5;
+            for (uint32_t e = threadIdx.x; e < 32 * ccol; e += TAB_THREADS) {
+                const uint32_t idx = (e & 31) * ccol + (e >> 5);
+                if (idx >= ne) continue;
+                const uint32_t ed = S.edges[idx];
                 ok &= tab_union(vpar, ed >> 16, ed & 0xFFFFu);
             }
             redo = !__syncthreads_and(ok);

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) k_gather(Work w) {
         for (int r = 0; r < ITEMS; ++r) {
             const uint32_t s = begin + r * 256 + threadIdx.x;
             if (s < end) {
-                w.spix[s] = px[r].x;                     // x | y << 16
+                w.spix[s] = clamp_pix(px[r].x, g.width, g.height);   // x | y << 16
                 w.stot[s] = (uint16_t)(px[r].y & 0xFFFFu);
             }
         }

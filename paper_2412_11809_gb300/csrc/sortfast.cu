@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
                 if (li < n_t) {
                     const uint32_t key = (uint32_t)(hit_toa(hv[r]) - base);
                     S.key[li] = key;
-                    S.pix[li] = hv[r].x;
+                    S.pix[li] = clamp_pix(hv[r].x, g.width, g.height);
                     S.tot[li] = (uint16_t)(hv[r].y & 0xFFFFu);
                     S.idx[li] = (uint16_t)li;
                     kmin = key < kmin ? key : kmin;

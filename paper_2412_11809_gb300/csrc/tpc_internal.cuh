@@ -227,6 +227,16 @@ __device__ __forceinline__ uint32_t hit_y(uint4 v) { return v.x >> 16; }
 __device__ __forceinline__ uint32_t hit_tot(uint4 v) { return v.y & 0xFFFFu; }
 __device__ __forceinline__ uint64_t hit_toa(uint4 v) { return ((uint64_t)v.w << 32) | v.z; }
 
+// Pixel clamped into the sensor.  k_prepare reports hits outside it (E_RANGE)
+// but the step still runs to its end, and the link kernels index per-pixel
+// tables with the sorted pixels, so the sorts store them clamped.
+__device__ __forceinline__ uint32_t clamp_pix(uint32_t pix, uint32_t W, uint32_t H) {
+    uint32_t x = pix & 0xFFFFu, y = pix >> 16;
+    x = x < W ? x : W - 1;
+    y = y < H ? y : H - 1;
+    return x | y << 16;
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers (one translation unit each)
 

@@ -126,6 +126,19 @@ def test_out_of_range_reported():
         assert e.value.name == "TPC_ERR_RANGE"
 
 
+def test_far_out_of_range_reported():
+    """Coordinates far outside the sensor: reported, and the per-pixel tables
+    of the link kernels are never indexed with them (pixels are clamped)."""
+    hits = oracle.make_hits([1, 65535, 3, 40000], [1, 65535, 2, 7], [5, 6, 7, 8])
+    for w, h in ((256, 256), (1024, 1024)):
+        with Clusterer(w, h, 128) as c:
+            c.push(hits)
+            c.flush()
+            with pytest.raises(TpcError) as e:
+                c.sync()
+            assert e.value.name == "TPC_ERR_RANGE"
+
+
 def test_span_too_large_reported():
     hits = oracle.make_hits([1, 2], [1, 1], [0, 2**33])
     with Clusterer(256, 256, 128) as c:
