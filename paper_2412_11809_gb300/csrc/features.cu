@@ -292,9 +292,11 @@ __global__ void __launch_bounds__(TILE_WORDS) k_records(Work w) {
                 rec.size = (int64_t)sl.size;
                 rec.sum_tot = (int64_t)sl.tot;
                 rec.first_toa = g.toa_min + skey[r];
-                const double sw = (double)sl.tot;
-                rec.cx = (float)((double)sl.wx / sw);
-                rec.cy = (float)((double)sl.wy / sw);
+                // fp32 quotient of the exact integer sums: three roundings, each
+                // at most 2^-24 relative (FP64 is a slow pipe on this GPU)
+                const float sw = (float)sl.tot;
+                rec.cx = (float)sl.wx / sw;
+                rec.cy = (float)sl.wy / sw;
                 g.out_rec[ord] = rec;
             }
             ++ord;

@@ -66,6 +66,28 @@ def test_pile_on_one_pixel():
     assert len(np.unique(lab)) == n
 
 
+def test_hot_pixel_mixes_table_and_general_tiles():
+    """A pixel hit far more often than the table link's list walk allows sends
+    the tiles of that burst to the general link kernel while the others stay
+    in table mode; clusters joining both kinds of tiles must come out exact."""
+    rng = np.random.default_rng(21)
+    bg = random_hits(rng, 60000, 64, 64, 120000)
+    n_hot = 1500
+    hot = oracle.make_hits(np.full(n_hot, 31), np.full(n_hot, 31),
+                           np.sort(rng.integers(50000, 56000, n_hot)), rng.integers(1, 20, n_hot))
+    hits = np.concatenate([bg, hot])
+    hits = hits[np.argsort(hits["toa"], kind="stable")]
+    lab, _ = check_against_oracle(hits, 64, 64, 500)
+    t_of = np.arange(len(hits)) // 4096
+    first = {}
+    spans = 0
+    for i, l in enumerate(lab):
+        if int(l) in first and first[int(l)] != t_of[i]:
+            spans += 1
+        first.setdefault(int(l), t_of[i])
+    assert spans > 100   # many clusters cross tile borders
+
+
 def test_all_same_toa_is_pixel_ccl():
     rng = np.random.default_rng(7)
     hits = random_hits(rng, 30000, 200, 150, 0)
