@@ -567,9 +567,44 @@ __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
         uint32_t s0, end;
         tile_range(g, t, s0, end);
         const uint32_t W = g.width, H = g.height, dt = g.dt, cw = (W + 3) >> 2;
-        // halo: [h0, s0) = earlier hits with key >= key(s0) - dt (a suffix)
         const uint32_t k0 = skey[s0];
         const uint32_t lo_key = k0 >= dt ? k0 - dt : 0;
+        const uint64_t hi64 = (uint64_t)skey[s0 - 1] + dt;
+        const uint32_t hi_key = hi64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)hi64;
+        {   // usual case: halo and front each within BORDER_THREADS positions of
+            // the border; one round trip stages both, the pairs run from
+            // shared memory
+            const uint32_t nwh = s0 - g.off < BORDER_THREADS ? s0 - g.off : BORDER_THREADS;
+            const uint32_t nwf = end - s0 < BORDER_THREADS ? end - s0 : BORDER_THREADS;
+            const uint32_t hb = s0 - nwh;
+            uint32_t fkey = 0, fpix = 0;
+            if (threadIdx.x < nwh) {
+                b_key[threadIdx.x] = skey[hb + threadIdx.x];
+                b_pix[threadIdx.x] = w.spix[hb + threadIdx.x];
+            }
+            if (threadIdx.x < nwf) {
+                fkey = skey[s0 + threadIdx.x];
+                fpix = w.spix[s0 + threadIdx.x];
+            }
+            __syncthreads();
+            const uint32_t nh = (uint32_t)__syncthreads_count(threadIdx.x < nwh && b_key[threadIdx.x] >= lo_key);
+            const uint32_t nf = (uint32_t)__syncthreads_count(threadIdx.x < nwf && fkey <= hi_key);
+            const bool halo_in = nh < nwh || hb == g.off, front_in = nf < nwf || s0 + nwf == end;
+            if (halo_in && front_in) {
+                if (threadIdx.x < nf) {
+                    const uint32_t i = s0 + threadIdx.x;
+                    for (uint32_t j = nwh; j-- > nwh - nh;) {
+                        if (fkey - b_key[j] > dt) break;
+                        if (adjacent(fpix, b_pix[j])) gunion(w.parent, i, hb + j);
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
+            __syncthreads();
+        }
+        // general case.  halo: [h0, s0) = earlier hits with key >= key(s0) - dt
+        // (a suffix)
         uint32_t h0 = s0;
         while (h0 > g.off) {
             const uint32_t chunk = h0 - g.off < BORDER_THREADS ? h0 - g.off : BORDER_THREADS;
@@ -581,8 +616,6 @@ __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
         }
         if (h0 == s0) continue;
         // front: [s0, e0) = tile hits with key <= key(s0 - 1) + dt (a prefix)
-        const uint64_t hi64 = (uint64_t)skey[s0 - 1] + dt;
-        const uint32_t hi_key = hi64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)hi64;
         uint32_t e0 = s0;
         while (e0 < end) {
             const uint32_t chunk = end - e0 < BORDER_THREADS ? end - e0 : BORDER_THREADS;
