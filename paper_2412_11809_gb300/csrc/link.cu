@@ -551,19 +551,119 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     }
 }
 
+// One warp per tile border, for the usual case of a halo and a front of at
+// most BF_WIN hits each: keys, pixels and tile roots of both are staged by
+// one round of loads, the halo and front counted with ballots, and every
+// (front, halo) pair within dt is checked from shared memory, newest halo
+// hit first.  An adjacent pair contributes the edge between the two hits'
+// tile roots (the tile links left every hit one step from its tile root);
+// each lane drops repeats of its previous edge and the warp then runs one
+// union per listed edge, so a dense border does not pay a chain of global
+// finds per pair.  Borders with a larger halo or front are listed for
+// k_border_link.
+constexpr int BF_WARPS = 8;
+constexpr int BF_WIN = 128;
+constexpr int BF_PER_LANE = BF_WIN / 32;
+constexpr int BF_EDGES = 64;
+
+__global__ void __launch_bounds__(BF_WARPS * 32, 4) k_border_fast(Work w) {
+    __shared__ uint32_t s_hk[BF_WARPS][BF_WIN];
+    __shared__ uint32_t s_hp[BF_WARPS][BF_WIN];
+    __shared__ uint32_t s_hr[BF_WARPS][BF_WIN];
+    __shared__ uint32_t s_ea[BF_WARPS][BF_EDGES], s_eb[BF_WARPS][BF_EDGES];
+    __shared__ uint32_t s_ne[BF_WARPS];
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *hk = s_hk[warp], *hp = s_hp[warp], *hr = s_hr[warp], *ea = s_ea[warp], *eb = s_eb[warp];
+    if (lane == 0) s_ne[warp] = 0;
+    __syncwarp();
+    for (uint32_t t = blockIdx.x * BF_WARPS + warp; t < nt; t += gridDim.x * BF_WARPS) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        if (t == g.tile0) continue;   // nothing before the segment's first tile
+        uint32_t s0, end;
+        tile_range(g, t, s0, end);
+        const uint32_t dt = g.dt;
+        const uint32_t nwh = s0 - g.off < (uint32_t)BF_WIN ? s0 - g.off : BF_WIN;
+        const uint32_t nwf = end - s0 < (uint32_t)BF_WIN ? end - s0 : BF_WIN;
+        const uint32_t hb = s0 - nwh;
+        uint32_t fk[BF_PER_LANE], fp[BF_PER_LANE], fr[BF_PER_LANE];
+#pragma unroll
+        for (int u = 0; u < BF_PER_LANE; ++u) {
+            const uint32_t j = u * 32 + lane;
+            if (j < nwh) {
+                hk[j] = skey[hb + j];
+                hp[j] = w.spix[hb + j];
+                hr[j] = w.parent[hb + j];
+            }
+            fk[u] = j < nwf ? skey[s0 + j] : 0xFFFFFFFFu;
+            fp[u] = j < nwf ? w.spix[s0 + j] : 0;
+            fr[u] = j < nwf ? w.parent[s0 + j] : 0;
+        }
+        __syncwarp();
+        const uint32_t k0 = __shfl_sync(0xffffffffu, fk[0], 0);
+        const uint32_t lo_key = k0 >= dt ? k0 - dt : 0;
+        const uint64_t hi64 = (uint64_t)hk[nwh - 1] + dt;
+        const uint32_t hi_key = hi64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)hi64;
+        uint32_t nh = 0, nf = 0;
+#pragma unroll
+        for (int u = 0; u < BF_PER_LANE; ++u) {
+            const uint32_t j = u * 32 + lane;
+            nh += __popc(__ballot_sync(0xffffffffu, j < nwh && hk[j] >= lo_key));
+            nf += __popc(__ballot_sync(0xffffffffu, j < nwf && fk[u] <= hi_key));
+        }
+        const bool halo_in = nh < nwh || hb == g.off, front_in = nf < nwf || s0 + nwf == end;
+        if (halo_in && front_in) {
+            uint32_t la = 0xFFFFFFFFu, lb = 0xFFFFFFFFu;   // this lane's previous edge
+#pragma unroll
+            for (int u = 0; u < BF_PER_LANE; ++u) {
+                const uint32_t j = u * 32 + lane;
+                if (j >= nf) continue;
+                const uint32_t key = fk[u], pix = fp[u], a = fr[u];
+                for (uint32_t h = nwh; h-- > nwh - nh;) {
+                    if (key - hk[h] > dt) break;
+                    if (!adjacent(pix, hp[h])) continue;
+                    const uint32_t b = hr[h];
+                    if (a == la && b == lb) continue;
+                    la = a;
+                    lb = b;
+                    const uint32_t slot = atomicAdd(&s_ne[warp], 1u);
+                    if (slot < (uint32_t)BF_EDGES) {
+                        ea[slot] = a;
+                        eb[slot] = b;
+                    } else {
+                        gunion(w.parent, a, b);
+                    }
+                }
+            }
+            __syncwarp();
+            const uint32_t ne = s_ne[warp] < (uint32_t)BF_EDGES ? s_ne[warp] : BF_EDGES;
+            for (uint32_t e = lane; e < ne; e += 32) gunion(w.parent, ea[e], eb[e]);
+        } else if (lane == 0) {
+            w.border_list[atomicAdd(&w.prob->border_count, 1u)] = t;
+        }
+        __syncwarp();   // the staging is rewritten for the next border
+        if (lane == 0) s_ne[warp] = 0;
+        __syncwarp();
+    }
+}
+
+// The borders k_border_fast listed: halo and front searched block-wide.
 __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
     __shared__ uint32_t b_key[HALO_BATCH];
     __shared__ uint32_t b_pix[HALO_BATCH];
+    __shared__ uint32_t b_root[HALO_BATCH];
     __shared__ uint32_t b_start[NBUCKETS + 1];
     __shared__ uint32_t b_cur[NBUCKETS];
     __shared__ uint32_t b_warp[32];
     __shared__ uint16_t b_seg[HALO_BATCH];
     const Prob &P = *w.prob;
-    const uint32_t nt = P.ntiles;
+    const uint32_t nlist = P.border_count;
     const uint32_t *skey = w.keys[sorted_sel(P)];
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    for (uint32_t u = blockIdx.x; u < nlist; u += gridDim.x) {
+        const uint32_t t = w.border_list[u];
         const Seg &g = w.seg[w.tile_seg[t]];
-        if (t == g.tile0) continue;   // nothing before the segment's first tile
         uint32_t s0, end;
         tile_range(g, t, s0, end);
         const uint32_t W = g.width, H = g.height, dt = g.dt, cw = (W + 3) >> 2;
@@ -571,40 +671,7 @@ __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
         const uint32_t lo_key = k0 >= dt ? k0 - dt : 0;
         const uint64_t hi64 = (uint64_t)skey[s0 - 1] + dt;
         const uint32_t hi_key = hi64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)hi64;
-        {   // usual case: halo and front each within BORDER_THREADS positions of
-            // the border; one round trip stages both, the pairs run from
-            // shared memory
-            const uint32_t nwh = s0 - g.off < BORDER_THREADS ? s0 - g.off : BORDER_THREADS;
-            const uint32_t nwf = end - s0 < BORDER_THREADS ? end - s0 : BORDER_THREADS;
-            const uint32_t hb = s0 - nwh;
-            uint32_t fkey = 0, fpix = 0;
-            if (threadIdx.x < nwh) {
-                b_key[threadIdx.x] = skey[hb + threadIdx.x];
-                b_pix[threadIdx.x] = w.spix[hb + threadIdx.x];
-            }
-            if (threadIdx.x < nwf) {
-                fkey = skey[s0 + threadIdx.x];
-                fpix = w.spix[s0 + threadIdx.x];
-            }
-            __syncthreads();
-            const uint32_t nh = (uint32_t)__syncthreads_count(threadIdx.x < nwh && b_key[threadIdx.x] >= lo_key);
-            const uint32_t nf = (uint32_t)__syncthreads_count(threadIdx.x < nwf && fkey <= hi_key);
-            const bool halo_in = nh < nwh || hb == g.off, front_in = nf < nwf || s0 + nwf == end;
-            if (halo_in && front_in) {
-                if (threadIdx.x < nf) {
-                    const uint32_t i = s0 + threadIdx.x;
-                    for (uint32_t j = nwh; j-- > nwh - nh;) {
-                        if (fkey - b_key[j] > dt) break;
-                        if (adjacent(fpix, b_pix[j])) gunion(w.parent, i, hb + j);
-                    }
-                }
-                __syncthreads();
-                continue;
-            }
-            __syncthreads();
-        }
-        // general case.  halo: [h0, s0) = earlier hits with key >= key(s0) - dt
-        // (a suffix)
+        // halo: [h0, s0) = earlier hits with key >= key(s0) - dt (a suffix)
         uint32_t h0 = s0;
         while (h0 > g.off) {
             const uint32_t chunk = h0 - g.off < BORDER_THREADS ? h0 - g.off : BORDER_THREADS;
@@ -625,34 +692,43 @@ __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
             e0 += cnt;
             if (cnt < chunk) break;
         }
+        // halo staged in batches with keys, pixels and tile roots; small
+        // borders scan every (front, halo) pair within dt, large ones bucket
+        // the batch by cell.  Unions join tile roots, skipping a repeat of
+        // the thread's previous one.
         const uint32_t nh = s0 - h0, nf = e0 - s0;
-        if (nh * (uint64_t)nf <= BORDER_PAIRS_DIRECT) {
-            // every (front, halo) pair within dt, newest halo hit first
-            for (uint32_t i = s0 + threadIdx.x; i < e0; i += BORDER_THREADS) {
-                const uint32_t key = skey[i], pix = w.spix[i];
-                for (uint32_t j = s0; j-- > h0;) {
-                    if (key - skey[j] > dt) break;
-                    if (adjacent(pix, w.spix[j])) gunion(w.parent, i, j);
-                }
-            }
-            continue;
-        }
+        const bool direct = nh * (uint64_t)nf <= BORDER_PAIRS_DIRECT;
         for (uint32_t hb = h0; hb < s0; hb += HALO_BATCH) {
             const uint32_t n_b = s0 - hb < HALO_BATCH ? s0 - hb : HALO_BATCH;
             for (uint32_t j = threadIdx.x; j < n_b; j += BORDER_THREADS) {
                 b_key[j] = skey[hb + j];
                 b_pix[j] = w.spix[hb + j];
+                b_root[j] = w.parent[hb + j];
             }
             __syncthreads();
-            bucket_sort(b_pix, n_b, cw, b_start, b_cur, b_seg, b_warp);
+            if (!direct) bucket_sort(b_pix, n_b, cw, b_start, b_cur, b_seg, b_warp);
             for (uint32_t i = s0 + threadIdx.x; i < e0; i += BORDER_THREADS) {
-                const uint32_t key = skey[i], pix = w.spix[i];
-                uint32_t b[4];
-                const int nb = neighbour_buckets(pix, W, H, cw, b);
-                for (int q2 = 0; q2 < nb; ++q2) {
-                    for (uint32_t q = b_start[b[q2]]; q < b_start[b[q2] + 1]; ++q) {
-                        const uint32_t j = b_seg[q];
-                        if (key - b_key[j] <= dt && adjacent(pix, b_pix[j])) gunion(w.parent, i, hb + j);
+                const uint32_t key = skey[i], pix = w.spix[i], a = w.parent[i];
+                uint32_t lb = 0xFFFFFFFFu;
+                if (direct) {   // newest halo hit first
+                    for (uint32_t j = n_b; j-- > 0;) {
+                        if (key - b_key[j] > dt) break;
+                        if (adjacent(pix, b_pix[j]) && b_root[j] != lb) {
+                            lb = b_root[j];
+                            gunion(w.parent, a, lb);
+                        }
+                    }
+                } else {
+                    uint32_t b[4];
+                    const int nb = neighbour_buckets(pix, W, H, cw, b);
+                    for (int q2 = 0; q2 < nb; ++q2) {
+                        for (uint32_t q = b_start[b[q2]]; q < b_start[b[q2] + 1]; ++q) {
+                            const uint32_t j = b_seg[q];
+                            if (key - b_key[j] <= dt && adjacent(pix, b_pix[j]) && b_root[j] != lb) {
+                                lb = b_root[j];
+                                gunion(w.parent, a, lb);
+                            }
+                        }
                     }
                 }
             }
@@ -713,6 +789,8 @@ void launch_tile_border(const Work &w, const Launch &L) {
     L.mark("k_tile_link_table");
     k_tile_link<<<L.fit(k_tile_link, LINK_THREADS, smem), LINK_THREADS, smem, L.stream>>>(w);
     L.mark("k_tile_link");
+    k_border_fast<<<L.fit(k_border_fast, BF_WARPS * 32, 0), BF_WARPS * 32, 0, L.stream>>>(w);
+    L.mark("k_border_fast");
     k_border_link<<<L.fit(k_border_link, BORDER_THREADS, 0), BORDER_THREADS, 0, L.stream>>>(w);
     L.mark("k_border_link");
 }

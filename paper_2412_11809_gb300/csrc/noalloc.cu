@@ -32,7 +32,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // byte offsets of every work array inside the scratch array
 struct Layout {
-    size_t seg, prob, tile_seg, redo, keys0, keys1, vals0, vals1, spix, stot, parent, root_of,
+    size_t seg, prob, tile_seg, redo, border_list, keys0, keys1, vals0, vals1, spix, stot, parent, root_of,
         slot, flag_label, flag_closed,
         tile_cnt, tile_base, hist, segtot, total;
 };
@@ -44,6 +44,7 @@ constexpr Layout make_layout() {
     l.prob = o; o += align256(sizeof(Prob));
     l.tile_seg = o; o += align256(NA_TILES * 4);
     l.redo = o; o += align256(NA_TILES * 4);
+    l.border_list = o; o += align256(NA_TILES * 4);
     l.keys0 = o; o += align256(NA_POS * 4);
     l.keys1 = o; o += align256(NA_POS * 4);
     l.vals0 = o; o += align256(NA_POS * 4);
@@ -140,6 +141,7 @@ extern "C" int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width,
     w.prob = reinterpret_cast<Prob *>(base + NA.prob);
     w.tile_seg = reinterpret_cast<uint32_t *>(base + NA.tile_seg);
     w.redo = reinterpret_cast<uint32_t *>(base + NA.redo);
+    w.border_list = reinterpret_cast<uint32_t *>(base + NA.border_list);
     w.keys[0] = reinterpret_cast<uint32_t *>(base + NA.keys0);
     w.keys[1] = reinterpret_cast<uint32_t *>(base + NA.keys1);
     w.vals[0] = reinterpret_cast<uint32_t *>(base + NA.vals0);

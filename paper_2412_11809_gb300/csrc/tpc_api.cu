@@ -70,7 +70,7 @@ struct Workspace {
         const size_t tiles = pos_cap / TILE + MAX_SEGS;
         // keys, vals (2 each), spix, parent, root_of: 4 B; stot: 2 B; slot; lab_tmp: 8 B
         return pos_cap * (7 * 4 + 2 + sizeof(Slot) + 8) + pos_cap / 4 +
-               tiles * (4 + 4 * 4 + RADIX * 4) + MAX_SEGS * (RADIX * 4 + sizeof(Seg)) + (1 << 16);
+               tiles * (4 + 4 + 4 * 4 + RADIX * 4) + MAX_SEGS * (RADIX * 4 + sizeof(Seg)) + (1 << 16);
     }
 
     cudaError_t ensure(size_t positions) {
@@ -88,6 +88,7 @@ struct Workspace {
         w.prob = mem.alloc<Prob>(1, e);
         w.tile_seg = mem.alloc<uint32_t>(T, e);
         w.redo = mem.alloc<uint32_t>(T, e);
+        w.border_list = mem.alloc<uint32_t>(T, e);
         w.keys[0] = mem.alloc<uint32_t>(P, e);
         w.keys[1] = mem.alloc<uint32_t>(P, e);
         w.vals[0] = mem.alloc<uint32_t>(P, e);

@@ -95,7 +95,7 @@ struct Prob {
     uint32_t fallback;     // the tile sort + merge did not order the input: radix sort
     uint32_t lsd_passes;   // passes the radix sort needs (max over segments)
     uint32_t redo_count;   // tiles the table-mode link left to the general link kernel
-    uint32_t pad;
+    uint32_t border_count; // tile borders k_border_fast left to k_border_link
 };
 
 // Feature sums of one cluster, kept at its root's sorted position.  One
@@ -115,6 +115,7 @@ struct Work {
     Seg *seg;
     Prob *prob;
     uint32_t *tile_seg;        // [tile_cap]
+    uint32_t *border_list;     // [tile_cap] tiles whose border needs the block-wide search
     uint32_t *redo;            // [tile_cap] tiles handed from table mode to k_tile_link
     uint32_t *keys[2];         // radix ping-pong: ToA - toa_min
     uint32_t *vals[2];         // radix ping-pong: position
