@@ -50,18 +50,21 @@ __device__ __forceinline__ uint32_t ls_match_digit(uint32_t d, uint32_t vmask) {
 
 struct LsShared {
     uint32_t key[TILE];
-    uint32_t pix[TILE];
-    uint16_t tot[TILE];
     uint16_t idx[TILE];          // local input index of the element at each rank
-    uint32_t wcnt[LS_WARPS][LS_RADIX];
-    uint32_t dstart[LS_RADIX];
+    uint16_t wcnt[LS_WARPS][LS_RADIX];
+    uint16_t dstart[LS_RADIX];
     uint32_t warp[32];
     uint32_t kmin[LS_WARPS], kmax[LS_WARPS];
 };
 
 constexpr int LS_SMEM = (int)sizeof(LsShared);
 
-__global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
+// Only keys and the permutation live in shared memory (four CTAs fit an SM,
+// as the registers allow); pixels and ToTs are fetched again at output, in
+// sorted order, from the tile just read (still in L2).  Per pass a thread
+// holds its 16 elements' local indices two to a register and each digit
+// with its rank among the warp's equal digits in one register.
+__global__ void __launch_bounds__(LS_THREADS, 4) k_tile_sort(Work w) {
     extern __shared__ __align__(16) unsigned char ls_raw[];
     LsShared &S = *reinterpret_cast<LsShared *>(ls_raw);
     const Prob &P = *w.prob;
@@ -79,20 +82,18 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
         constexpr int HALF = LS_ITEMS / 2;   // two batches of loads keep registers in bounds
 #pragma unroll
         for (int hb = 0; hb < 2; ++hb) {
-            uint4 hv[HALF];
+            uint2 tv[HALF];   // ToA words of each hit
 #pragma unroll
             for (int r = 0; r < HALF; ++r) {
                 const uint32_t li = (hb * HALF + r) * LS_THREADS + threadIdx.x;
-                if (li < n_t) hv[r] = ld_hit(hits + li);
+                if (li < n_t) tv[r] = __ldg(reinterpret_cast<const uint2 *>(hits + li) + 1);
             }
 #pragma unroll
             for (int r = 0; r < HALF; ++r) {
                 const uint32_t li = (hb * HALF + r) * LS_THREADS + threadIdx.x;
                 if (li < n_t) {
-                    const uint32_t key = (uint32_t)(hit_toa(hv[r]) - base);
+                    const uint32_t key = (uint32_t)((((uint64_t)tv[r].y << 32) | tv[r].x) - base);
                     S.key[li] = key;
-                    S.pix[li] = clamp_pix(hv[r].x, g.width, g.height);
-                    S.tot[li] = (uint16_t)(hv[r].y & 0xFFFFu);
                     S.idx[li] = (uint16_t)li;
                     kmin = key < kmin ? key : kmin;
                     kmax = key > kmax ? key : kmax;
@@ -113,29 +114,29 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
 
         for (int pass = 0; pass < passes; ++pass) {
             const int shift = pass * LS_BITS;
-            uint32_t kk[LS_ITEMS];
-            uint16_t ii[LS_ITEMS];
-            uint32_t rr[LS_ITEMS];
+            uint32_t ii2[LS_ITEMS / 2];   // local indices, two per register
+            uint32_t dr[LS_ITEMS];        // digit << 16 | rank among the warp's equal digits
 #pragma unroll
             for (int r = 0; r < LS_ITEMS; ++r) {
                 const uint32_t e = warp * LS_WARP_SPAN + r * 32 + lane;
-                ii[r] = S.idx[e];
-                kk[r] = ii[r] == LS_NONE ? 0 : S.key[ii[r]];
+                const uint32_t i = S.idx[e];
+                if (r & 1) ii2[r >> 1] |= i << 16; else ii2[r >> 1] = i;
+                // padding sorts last: digit RADIX-1 in every pass, after all real entries
+                dr[r] = i == LS_NONE ? LS_RADIX - 1 : ((S.key[i] - kmin) >> shift) & (LS_RADIX - 1);
             }
-            for (int i = threadIdx.x; i < LS_WARPS * LS_RADIX; i += LS_THREADS) (&S.wcnt[0][0])[i] = 0;
+            for (int i = threadIdx.x; i < LS_WARPS * LS_RADIX / 2; i += LS_THREADS)
+                reinterpret_cast<uint32_t *>(&S.wcnt[0][0])[i] = 0;
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < LS_ITEMS; ++r) {
-                // padding sorts last: digit RADIX-1 in every pass, after all real entries
-                const uint32_t d = ii[r] == LS_NONE ? LS_RADIX - 1 : ((kk[r] - kmin) >> shift) & (LS_RADIX - 1);
+                const uint32_t d = dr[r];
                 const uint32_t peers = ls_match_digit(d, 0xffffffffu);
                 const uint32_t rank = __popc(peers & lt);
                 const uint32_t pre = S.wcnt[warp][d];
                 __syncwarp();
-                if (rank == 0) S.wcnt[warp][d] = pre + __popc(peers);
+                if (rank == 0) S.wcnt[warp][d] = (uint16_t)(pre + __popc(peers));
                 __syncwarp();
-                rr[r] = pre + rank;
-                kk[r] = d;   // keep the digit
+                dr[r] = d << 16 | (pre + rank);
             }
             __syncthreads();
             {   // per digit: prefix over warps; then exclusive scan of the digit totals
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
 #pragma unroll
                     for (int q = 0; q < LS_WARPS; ++q) {
                         const uint32_t c = S.wcnt[q][d0 + u];
-                        S.wcnt[q][d0 + u] = sum;
+                        S.wcnt[q][d0 + u] = (uint16_t)sum;
                         sum += c;
                     }
                     tot2[u] = sum;
@@ -163,23 +164,25 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
                 __syncthreads();
                 uint32_t pre = 0;
                 for (int q = 0; q < warp; ++q) pre += S.warp[q];
-                S.dstart[d0] = pre + x - both;
-                S.dstart[d0 + 1] = pre + x - both + tot2[0];
+                S.dstart[d0] = (uint16_t)(pre + x - both);
+                S.dstart[d0 + 1] = (uint16_t)(pre + x - both + tot2[0]);
             }
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < LS_ITEMS; ++r) {
-                const uint32_t d = kk[r];
-                S.idx[S.dstart[d] + S.wcnt[warp][d] + rr[r]] = ii[r];
+                const uint32_t d = dr[r] >> 16;
+                const uint32_t i = (ii2[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu;
+                S.idx[S.dstart[d] + S.wcnt[warp][d] + (dr[r] & 0xFFFFu)] = (uint16_t)i;
             }
             __syncthreads();
         }
         for (uint32_t j = threadIdx.x; j < n_t; j += LS_THREADS) {
             const uint32_t li = S.idx[j];
+            const uint2 px = __ldg(reinterpret_cast<const uint2 *>(hits + li));   // x | y << 16, ToT
             w.keys[0][begin + j] = S.key[li];
             w.vals[0][begin + j] = begin + li;
-            w.spix[begin + j] = S.pix[li];
-            w.stot[begin + j] = S.tot[li];
+            w.spix[begin + j] = clamp_pix(px.x, g.width, g.height);
+            w.stot[begin + j] = (uint16_t)(px.y & 0xFFFFu);
         }
         __syncthreads();
     }
