@@ -105,37 +105,51 @@ def measured_peak_gbs() -> tuple[float, str]:
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock/throttle samples, every 50 ms from before the warm-up;
+    summary() keeps the samples taken inside the timed window (host wall clock
+    around the timed steps), else the nearest one on each side of it."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
+        self.window = None
+        self.out = ""
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         return self
 
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
+
     def __exit__(self, *exc):
-        self.out = ""
         if self.proc is not None:
+            time.sleep(0.15)   # let a sample after the window arrive
             self.proc.terminate()
             try:
                 self.out, _ = self.proc.communicate(timeout=5)
             except Exception:
                 self.proc.kill()
 
+    @staticmethod
+    def _stamp(v: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(v.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def summary(self) -> dict:
-        rows = [r for r in csv.reader(io.StringIO(getattr(self, "out", "")))
-                if len(r) >= 9]
+        rows = [r for r in csv.reader(io.StringIO(self.out)) if len(r) >= 10]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         def num(v):
@@ -143,17 +157,29 @@ class ClockSampler:
                 return float(v)
             except ValueError:
                 return None
-        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
-        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        where = "timed window"
+        if self.window is not None:
+            t0, t1 = self.window
+            stamped = [(self._stamp(r[0]), r) for r in rows]
+            inside = [r for ts, r in stamped if ts is not None and t0 <= ts <= t1]
+            if not inside:   # a window shorter than the sampling period
+                before = [(ts, r) for ts, r in stamped if ts is not None and ts < t0]
+                after = [(ts, r) for ts, r in stamped if ts is not None and ts > t1]
+                inside = ([max(before, key=lambda x: x[0])[1]] if before else []) + \
+                         ([min(after, key=lambda x: x[0])[1]] if after else [])
+                where = "nearest samples around a timed window shorter than the 50 ms period"
+            rows = inside or rows
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        smax = [num(r[3]) for r in rows if num(r[3]) is not None]
         reasons = set()
         for r in rows:
             for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
-                                "sw_power_cap"), r[5:9]):
+                                "sw_power_cap"), r[6:10]):
                 if v.strip().lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "sampled": where}
 
 
 def dist_info():
@@ -360,16 +386,18 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        n_clusters = step_device()
-    barrier()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
+        for _ in range(args.warmup):
+            n_clusters = step_device()
+        barrier()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_host0 = time.time()
         start.record(stream)
         for _ in range(args.steps):
             n_clusters = step_device()
         end.record(stream)
         end.synchronize()
+        clocks.mark(t_host0, time.time())
     barrier()
     ms = start.elapsed_time(end)
     t = torch.tensor([ms], device=dev)
@@ -395,32 +423,64 @@ def run_gpu(args):
     b_alg = path_bytes_per_hit(n, n_clusters)
     path_gbs = value / world * b_alg / 1e9
 
-    # end to end: pinned host input, host results, through the same API
+    # end to end: pinned host input, host results, through the same API.  Two
+    # contexts on two CUDA streams take the steps in turn, so one step's copies
+    # overlap the other's kernels: a step's input copy, kernels and label copy
+    # are queued without waiting (tpc_labels_async), and its records are
+    # fetched after the next step is queued (fetching them returns their
+    # count, which waits for that step).
     pin_in = host_u8.pin_memory()
-    pin_lab = torch.empty(n, dtype=torch.int64).pin_memory()
-    pin_rec = torch.empty((n, CLUSTER_DTYPE.itemsize), dtype=torch.uint8).pin_memory()
+    stream2 = torch.cuda.Stream(device=dev)
+    ctxs = [c, Clusterer(W, H, DT, stream=stream2)]
+    pin_lab = [torch.empty(n, dtype=torch.int64).pin_memory() for _ in ctxs]
+    pin_rec = [torch.empty((n, CLUSTER_DTYPE.itemsize), dtype=torch.uint8).pin_memory() for _ in ctxs]
 
-    def step_e2e():
-        c.push_ptr(pin_in.data_ptr(), n, device=False)
-        c.flush()
-        c.labels_into(pin_lab.data_ptr(), n, device=False)
-        return c.features_into(pin_rec.data_ptr(), n, device=False)
+    def issue(k):   # nothing here waits for the device
+        cx = ctxs[k % 2]
+        cx.push_ptr(pin_in.data_ptr(), n, device=False)
+        cx.flush()
+        cx.labels_async(pin_lab[k % 2].data_ptr(), n, device=False)
 
-    for _ in range(max(1, args.warmup)):
-        step_e2e()
+    def finish(k):
+        return ctxs[k % 2].features_into(pin_rec[k % 2].data_ptr(), n, device=False)
+
+    e2e_steps = max(2, min(args.steps, 10))
+    for k in range(max(2, args.warmup)):
+        issue(k)
+        finish(k)
     barrier()
-    e2e_steps = max(1, min(args.steps, 5))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        m = step_e2e()
-    e1.record(stream)
-    e1.synchronize()
+    s_a, s_b = stream, stream2
+    e0 = torch.cuda.Event(enable_timing=True)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s_a)
+    s_b.wait_event(e0)
+    m = 0
+    for k in range(e2e_steps):
+        issue(k)
+        if k:
+            m = finish(k - 1)
+    m = finish(e2e_steps - 1)
+    ea.record(s_a)
+    eb.record(s_b)
+    ea.synchronize()
+    eb.synchronize()
     barrier()
-    te = torch.tensor([e0.elapsed_time(e1)], device=dev)
+    te = torch.tensor([max(e0.elapsed_time(ea), e0.elapsed_time(eb))], device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = n * world * e2e_steps / (float(te.item()) / 1e3)
+    ctxs[1].close()
+
+    # the link itself: one pinned H2D of the step's input, one D2H of its labels
+    link = {}
+    for name, dst, src in (("h2d_gbs", d_hits, pin_in), ("d2h_gbs", pin_lab[0], d_labels)):
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            l0.record(stream)
+            dst.copy_(src.view(dst.dtype).reshape(dst.shape), non_blocking=True)
+            l1.record(stream)
+        l1.synchronize()
+        link[name] = dst.numel() * dst.element_size() / (l0.elapsed_time(l1) / 1e3) / 1e9
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -454,7 +514,9 @@ def run_gpu(args):
             "kernel_ms": prof_ms,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "hits/s", "h2d_bytes_per_step": 16 * n,
-                    "d2h_bytes_per_step": 8 * n + CLUSTER_DTYPE.itemsize * m},
+                    "d2h_bytes_per_step": 8 * n + CLUSTER_DTYPE.itemsize * m,
+                    "pipelining": "two contexts on two CUDA streams, steps alternating",
+                    "link_gbs": link},
             "gpu_launches": n_kernels * args.steps,
             "clocks": clocks.summary(),
             "serving": serving,
@@ -470,7 +532,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 64 Mi-hit stream")

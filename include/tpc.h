@@ -136,6 +136,19 @@ int tpc_sync(tpc_ctx *ctx);
 int tpc_labels(tpc_ctx *ctx, uint64_t *labels, uint64_t *indices, size_t cap,
                size_t *n_out, int where);
 
+/* Queue, without waiting, the copy of the labels of the last one-shot step
+   (tpc_flush or tpc_batch_flush of a non-streaming context) into `labels`
+   (at least cap entries in `where` memory), on the context stream.  After
+   push...push, flush these are the labels of every hit pushed since the
+   previous flush, in push order, so their number is known on the host
+   without reading the device; *n_out receives it.  The buffer holds the
+   labels once tpc_sync() or a later retrieval call on the context has
+   returned, and device-side errors of the step are reported there.  Lets a
+   caller overlap one step's copies with another context's kernels.
+   TPC_ERR_STATE for a streaming result or before the first step;
+   TPC_ERR_CAP (nothing queued) if cap < *n_out. */
+int tpc_labels_async(tpc_ctx *ctx, uint64_t *labels, size_t cap, size_t *n_out, int where);
+
 /* Cluster records finalised by the last processing step, ordered by label.
    Same size protocol as tpc_labels. */
 int tpc_cluster_features(tpc_ctx *ctx, tpc_cluster *out, size_t cap, size_t *n_out,

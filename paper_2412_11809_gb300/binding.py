@@ -37,6 +37,7 @@ SIGNATURES = {
     "tpc_flush": ([_VP], _INT),
     "tpc_sync": ([_VP], _INT),
     "tpc_labels": ([_VP, _VP, _VP, _SZ, ctypes.POINTER(_SZ), _INT], _INT),
+    "tpc_labels_async": ([_VP, _VP, _SZ, ctypes.POINTER(_SZ), _INT], _INT),
     "tpc_cluster_features": ([_VP, _VP, _SZ, ctypes.POINTER(_SZ), _INT], _INT),
     "tpc_batch_flush": ([ctypes.POINTER(_VP), _INT], _INT),
     "tpc_counts": ([_VP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)], _INT),
@@ -154,6 +155,14 @@ class Clusterer:
                                   TPC_DEVICE if device else TPC_HOST)
         self._keep.clear()
         _check(rc, "tpc_labels")
+        return n_out.value
+
+    def labels_async(self, labels_ptr: int, cap: int, device: bool) -> int:
+        """Queue the copy of the last one-shot step's labels (valid after sync()
+        or the next retrieval); returns their count."""
+        n_out = ctypes.c_size_t()
+        _check(self._lib.tpc_labels_async(self._h, labels_ptr, cap, ctypes.byref(n_out),
+                                          TPC_DEVICE if device else TPC_HOST), "tpc_labels_async")
         return n_out.value
 
     def features_into(self, rec_ptr: int, cap: int, device: bool) -> int:

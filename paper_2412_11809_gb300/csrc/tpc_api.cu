@@ -788,6 +788,20 @@ int tpc_labels(tpc_ctx *c, uint64_t *labels, uint64_t *indices, size_t cap, size
     return cudaStreamSynchronize(c->stream) == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }
 
+int tpc_labels_async(tpc_ctx *c, uint64_t *labels, size_t cap, size_t *n_out, int where) {
+    if (!c || !n_out || (where != TPC_HOST && where != TPC_DEVICE)) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->has_result || c->res_streaming) return TPC_ERR_STATE;
+    const size_t n = c->pushed - c->res_base;   // every hit of a one-shot step is final
+    *n_out = n;
+    if (n > cap) return TPC_ERR_CAP;
+    if (!n) return TPC_OK;
+    if (!labels) return TPC_ERR_ARG;
+    const cudaMemcpyKind kind = where == TPC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    return cudaMemcpyAsync(labels, c->d_labels, n * sizeof(uint64_t), kind, c->stream) == cudaSuccess
+               ? TPC_OK : TPC_ERR_CUDA;
+}
+
 int tpc_cluster_features(tpc_ctx *c, tpc_cluster *out, size_t cap, size_t *n_out, int where) {
     if (!c || !n_out || (where != TPC_HOST && where != TPC_DEVICE)) return TPC_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);

@@ -217,3 +217,44 @@ def test_cfg1_full_size_sampled():
     checked = sampled_cluster_check(hits, lab, 256, 256, synth.DT_200NS, 150,
                                     np.random.default_rng(1))
     assert checked > 50
+
+
+def test_labels_async_and_two_context_pipeline():
+    """Queued label copies (tpc_labels_async) equal the synchronous ones, also
+    when two contexts on two CUDA streams take steps in turn and one step's
+    copies overlap the other's kernels."""
+    hits, _ = synth.cfg0(scale=0.05, seed=9)
+    n = len(hits)
+    want = oracle.labels(hits, 256, 256, 128)
+    want_rec = oracle.features(hits, want)
+    pin_in = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).pin_memory()
+    ctxs = [Clusterer(256, 256, 128, stream=torch.cuda.Stream()) for _ in range(2)]
+    bufs = [torch.empty(n, dtype=torch.int64).pin_memory() for _ in ctxs]
+    def shifted(rec, base):   # labels are global indices: a context's k-th step adds k * n
+        rec = rec.copy()
+        rec["label"] += base
+        return rec
+
+    try:
+        for step in range(4):
+            c = ctxs[step % 2]
+            c.push_ptr(pin_in.data_ptr(), n, device=False)
+            c.flush()
+            assert c.labels_async(bufs[step % 2].data_ptr(), n, device=False) == n
+            if step:
+                prev, base = ctxs[(step - 1) % 2], n * ((step - 1) // 2)
+                assert_features_equal(prev.features(), shifted(want_rec, base))   # waits for that step
+                np.testing.assert_array_equal(bufs[(step - 1) % 2].numpy(), want + base)
+        ctxs[1].sync()
+        np.testing.assert_array_equal(bufs[1].numpy(), want + n)
+        with pytest.raises(TpcError) as e:
+            ctxs[0].labels_async(bufs[0].data_ptr(), n - 1, device=False)
+        assert e.value.name == "TPC_ERR_CAP"
+    finally:
+        for c in ctxs:
+            c.close()
+    with Clusterer(256, 256, 128, max_disorder=10**6) as c:
+        c.push(hits[:1000])
+        with pytest.raises(TpcError) as e:
+            c.labels_async(bufs[0].data_ptr(), n, device=False)
+        assert e.value.name == "TPC_ERR_STATE"
