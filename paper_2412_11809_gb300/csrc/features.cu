@@ -21,7 +21,7 @@ namespace tpc {
 constexpr int ACC_THREADS = 512;
 constexpr int ACC_SPAN = 2048;                    // sorted positions per pass
 constexpr int ACC_ITEMS = ACC_SPAN / ACC_THREADS;
-constexpr int ACC_SMEM = 4 * ACC_SPAN * (int)sizeof(uint32_t) + 2 * ACC_SPAN * (int)sizeof(unsigned long long);
+constexpr int ACC_SMEM = 2 * ACC_SPAN * (int)sizeof(uint32_t) + 3 * ACC_SPAN * (int)sizeof(unsigned long long);
 
 // Roots and features in (ToA, position) order, where a cluster's hits sit
 // close together.  Each pass over ACC_SPAN sorted positions finds every
@@ -32,13 +32,16 @@ constexpr int ACC_SMEM = 4 * ACC_SPAN * (int)sizeof(uint32_t) + 2 * ACC_SPAN * (
 // redux), so a burst of one track does not serialise on one slot.  One
 // partial per root then goes to the global slots; hits whose root lies
 // before the span go there directly.  The global slots of tile roots were
-// zeroed by the tile-link kernels.
+// zeroed by the tile-link kernels.  Size and sum ToT share one 64-bit
+// shared-memory counter (size << 32 | sum ToT: a span holds at most ACC_SPAN
+// hits of ToT < 2^16, so neither part overflows), and the last key is kept
+// only when a streaming watermark needs it.
 __global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
     extern __shared__ __align__(16) unsigned char acc_raw[];
     unsigned long long *a_wx = reinterpret_cast<unsigned long long *>(acc_raw);
-    unsigned long long *a_wy = a_wx + ACC_SPAN;
-    uint32_t *a_size = reinterpret_cast<uint32_t *>(a_wy + ACC_SPAN), *a_tot = a_size + ACC_SPAN,
-             *a_min = a_size + 2 * ACC_SPAN, *a_max = a_size + 3 * ACC_SPAN;
+    unsigned long long *a_wy = a_wx + ACC_SPAN, *a_st = a_wy + ACC_SPAN;
+    uint32_t *a_min = reinterpret_cast<uint32_t *>(a_st + ACC_SPAN), *a_max = a_min + ACC_SPAN;
+    static_assert((unsigned long long)ACC_SPAN * 0xFFFFu < (1ull << 32), "packed sum ToT fits 32 bits");
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
@@ -48,6 +51,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
+        const bool want_max = g.close_mode == CLOSE_WM;
         for (uint32_t b = begin; b < end; b += ACC_SPAN) {
             const uint32_t e = b + ACC_SPAN < end ? b + ACC_SPAN : end;
             uint32_t rr[ACC_ITEMS], px[ACC_ITEMS], tt[ACC_ITEMS], kk[ACC_ITEMS], ps[ACC_ITEMS];
@@ -79,8 +83,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
                 w.root_of[ps[q]] = r;
                 if (r == s) {
                     const uint32_t k = s - b;
-                    a_size[k] = a_tot[k] = 0;
-                    a_wx[k] = a_wy[k] = 0;
+                    a_st[k] = a_wx[k] = a_wy[k] = 0;
                     a_min[k] = 0xFFFFFFFFu;
                     a_max[k] = 0;
                 }
@@ -106,17 +109,16 @@ __global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
                     wy = ((unsigned long long)__reduce_add_sync(peers, wy32 >> 16) << 16) +
                          __reduce_add_sync(peers, wy32 & 0xFFFFu);
                     mn = __reduce_min_sync(peers, mn);
-                    mx = __reduce_max_sync(peers, mx);
+                    if (want_max) mx = __reduce_max_sync(peers, mx);
                 }
                 if (lane != __ffs(peers) - 1) continue;
                 if (r >= b) {
                     const uint32_t k = r - b;
-                    atomicAdd(&a_size[k], cnt);
-                    atomicAdd(&a_tot[k], sum_tot);
+                    atomicAdd(&a_st[k], (unsigned long long)cnt << 32 | sum_tot);
                     atomicAdd(&a_wx[k], wx);
                     atomicAdd(&a_wy[k], wy);
                     atomicMin(&a_min[k], mn);
-                    atomicMax(&a_max[k], mx);
+                    if (want_max) atomicMax(&a_max[k], mx);
                 } else {
                     Slot &sl = w.slot[r];
                     atomicAdd(&sl.size, cnt);
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
                     atomicAdd(&sl.wx, wx);
                     atomicAdd(&sl.wy, wy);
                     atomicMin(&sl.min, mn);
-                    atomicMax(&sl.maxkey, mx);
+                    if (want_max) atomicMax(&sl.maxkey, mx);
                 }
             }
             __syncthreads();
@@ -134,12 +136,13 @@ __global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
                 const uint32_t r = b + k;
                 if (r < e && rr[q] == r) {
                     Slot &sl = w.slot[r];
-                    atomicAdd(&sl.size, a_size[k]);
-                    atomicAdd(&sl.tot, (unsigned long long)a_tot[k]);
+                    const unsigned long long st = a_st[k];
+                    atomicAdd(&sl.size, (uint32_t)(st >> 32));
+                    atomicAdd(&sl.tot, st & 0xFFFFFFFFull);
                     atomicAdd(&sl.wx, a_wx[k]);
                     atomicAdd(&sl.wy, a_wy[k]);
                     atomicMin(&sl.min, a_min[k]);
-                    atomicMax(&sl.maxkey, a_max[k]);
+                    if (want_max) atomicMax(&sl.maxkey, a_max[k]);
                 }
             }
             __syncthreads();

@@ -461,8 +461,9 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                     }
                 };
                 // heads of the 9 lists first (independent loads), then the head
-                // entries without loops; lists with a second entry (a pixel hit
-                // more than once in the tile: rare) are walked afterwards
+                // entries without loops or branches around the loads; lists
+                // with a second entry (a pixel hit more than once in the tile:
+                // rare) are walked afterwards
                 uint32_t hd[9];
 #pragma unroll
                 for (int n = 0; n < 9; ++n) hd[n] = S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)];
@@ -470,11 +471,11 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
 #pragma unroll
                 for (int n = 0; n < 9; ++n) {
                     const uint32_t j = hd[n];
-                    if (j != TAB_NONE) {
-                        const uint32_t kj = S.key[j];
-                        more |= (S.next[j] != TAB_NONE ? 1u : 0u) << n;
-                        if (j < k && key - kj <= dt) consider(j);
-                    }
+                    const uint32_t jm = j & (TILE - 1);   // an empty head reads a harmless entry
+                    const uint32_t kj = S.key[jm], nx = S.next[jm];
+                    const bool has = j != TAB_NONE;
+                    more |= (has && nx != TAB_NONE ? 1u : 0u) << n;
+                    if (has && j < k && key - kj <= dt) consider(j);
                 }
                 while (more) {   // lists holding more than one hit
                     const int n = __ffs(more) - 1;
