@@ -34,12 +34,20 @@ namespace tpc {
 
 constexpr int LINK_THREADS = 512;
 constexpr uint32_t TAB_CAP = 68u << 10;        // table entries: sensor plus a 1-pixel frame
+constexpr uint32_t TAB_MAX_BANDS = 16;
 
-// Table mode: the sensor with a frame of empty pixels around it fits the
-// shared-memory table (a 256 x 256 sensor takes 258 x 258 entries).
-__device__ __forceinline__ bool table_mode(uint32_t W, uint32_t H) {
-    return (uint64_t)(W + 2) * (H + 2) <= TAB_CAP;
+// Table mode: the sensor, with a frame of empty pixels around it, is covered
+// by the shared-memory table in at most TAB_MAX_BANDS bands of rows (one band
+// for a 256 x 256 sensor, 258 x 258 entries; four for 448 x 512).  Rows per
+// band (a band's table also holds the row above and the row below it);
+// 0 when the sensor does not qualify.
+__device__ __forceinline__ uint32_t table_rows(uint32_t W, uint32_t H) {
+    const uint32_t W2 = W + 2;
+    if (W2 * 3 > TAB_CAP) return 0;
+    const uint32_t rpb = TAB_CAP / W2 - 2;
+    return (H + rpb - 1) / rpb <= TAB_MAX_BANDS ? rpb : 0;
 }
+__device__ __forceinline__ bool table_mode(uint32_t W, uint32_t H) { return table_rows(W, H) != 0; }
 constexpr int NBUCKETS = 2048;                // hashed 4x4-pixel cells
 constexpr int HALO_BATCH = 2048;
 constexpr int BORDER_THREADS = 256;
@@ -337,7 +345,8 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
 constexpr int TAB_THREADS = 1024;
 constexpr uint16_t TAB_NONE = 0xFFFFu;
 constexpr int TAB_WALK = 64;
-constexpr int TAB_EDGES = 2 * TILE;
+constexpr int TAB_EDGES = 3 * TILE / 2;
+constexpr int CAND = 6;
 
 struct TabShared {
     uint16_t tab[TAB_CAP];           // head of each pixel's list (rank), or TAB_NONE
@@ -345,6 +354,9 @@ struct TabShared {
     uint16_t next[TILE];             // per rank: next rank on the same pixel
     uint32_t par[TILE];              // forest over ranks
     uint32_t edges[TAB_EDGES];       // extra edges, k << 16 | j
+    uint32_t pix[TILE];              // per rank: pixel (banded sensors)
+    uint16_t wl[TILE];               // ranks walked in the current band
+    uint32_t wl_count[TAB_MAX_BANDS];
     uint32_t nedges;
     uint32_t overflow;
 };
@@ -398,6 +410,72 @@ __device__ __forceinline__ bool tab_union(volatile uint32_t *par, uint32_t a, ui
     return false;
 }
 
+// The walk of hit k (key `key`; `centre` = its pixel's table entry, rows W2
+// entries apart): its smallest earlier neighbour within dt becomes `parent`,
+// further ones go to cand[] (more than CAND straight to the edge list).  The
+// heads of the 9 lists are read first (independent loads), then the head
+// entries without loops or branches around the loads; lists with a second
+// entry (a pixel hit more than once in the tile: rare) are walked afterwards.
+__device__ __forceinline__ void tab_walk(TabShared &S, uint32_t k, uint32_t key, uint32_t centre,
+                                         uint32_t W2, uint32_t dt, uint32_t &parent,
+                                         uint32_t (&cand)[CAND], int &nc) {
+    auto consider = [&](uint32_t j) {   // j: an earlier neighbour within dt
+        uint32_t other = j;
+        if (parent == k) { parent = j; return; }
+        if (j < parent) { other = parent; parent = j; }
+        if (nc < CAND) {   // constant indices keep cand in registers
+#pragma unroll
+            for (int i = 0; i < CAND; ++i)
+                if (i == nc) cand[i] = other;
+            ++nc;
+        } else {   // rare: straight to the edge list
+            const uint32_t slot = atomicAdd(&S.nedges, 1u);
+            if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | other;
+        }
+    };
+    uint32_t hd[9];
+#pragma unroll
+    for (int n = 0; n < 9; ++n) hd[n] = S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)];
+    uint32_t more = 0;
+#pragma unroll
+    for (int n = 0; n < 9; ++n) {
+        const uint32_t j = hd[n];
+        const uint32_t jm = j & (TILE - 1);   // an empty head reads a harmless entry
+        const uint32_t kj = S.key[jm], nx = S.next[jm];
+        const bool has = j != TAB_NONE;
+        more |= (has && nx != TAB_NONE ? 1u : 0u) << n;
+        if (has && j < k && key - kj <= dt) consider(j);
+    }
+    while (more) {   // lists holding more than one hit
+        const int n = __ffs(more) - 1;
+        more &= more - 1;
+        uint32_t j = S.next[S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)]];
+        int steps = 1;
+        for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps)
+            if (j < k && key - S.key[j] <= dt) consider(j);
+        if (j != TAB_NONE) S.overflow = 1;
+    }
+}
+
+// Append the warp's candidate edges to the shared list; every lane calls
+// this (a ballot per candidate slot).
+__device__ __forceinline__ void tab_append(TabShared &S, uint32_t k, const uint32_t (&cand)[CAND], int nc,
+                                           int lane) {
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t most = __reduce_max_sync(0xffffffffu, (uint32_t)nc);
+#pragma unroll
+    for (int c = 0; c < CAND; ++c) {
+        if (c >= (int)most) break;
+        const bool has = c < nc;
+        const uint32_t m = __ballot_sync(0xffffffffu, has);
+        uint32_t slot0 = 0;
+        if (lane == 0) slot0 = atomicAdd(&S.nedges, (uint32_t)__popc(m));
+        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+        const uint32_t slot = slot0 + __popc(m & lt_mask);
+        if (has && slot < TAB_EDGES) S.edges[slot] = (k << 16) | cand[c];
+    }
+}
+
 __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     extern __shared__ __align__(16) unsigned char tab_raw[];
     TabShared &S = *reinterpret_cast<TabShared *>(tab_raw);
@@ -412,7 +490,9 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         const uint32_t W = g.width, H = g.height, dt = g.dt;
-        if (!table_mode(W, H)) continue;   // k_tile_link handles larger sensors
+        const uint32_t rpb = table_rows(W, H);
+        if (!rpb) continue;   // k_tile_link handles sensors the table cannot cover
+        const uint32_t nb = (H + rpb - 1) / rpb, W2 = W + 2;
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         const uint32_t n_t = end - begin;
@@ -424,81 +504,80 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             if (k < n_t) { kv[q] = skey[begin + k]; pv[q] = w.spix[begin + k]; }
         }
         if (threadIdx.x == 0) { S.overflow = 0; S.nedges = 0; }
+        if (nb == 1) {
+            // the whole sensor in one table: push every hit, then walk each
+            // from registers
 #pragma unroll
-        for (int q = 0; q < ITEMS; ++q) {
-            const uint32_t k = q * TAB_THREADS + threadIdx.x;
-            if (k < n_t) {
-                S.key[k] = kv[q];
-                S.next[k] = tab_push(S.tab, tab_pid(pv[q], W), (uint16_t)k);
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                if (k < n_t) {
+                    S.key[k] = kv[q];
+                    S.next[k] = tab_push(S.tab, tab_pid(pv[q], W), (uint16_t)k);
+                }
             }
-        }
-        __syncthreads();
-        // neighbour walk: smallest earlier neighbour = parent, the others =
-        // edges, gathered in registers and appended warp by warp (ballots)
-        constexpr int CAND = 6;
-        const uint32_t lt_mask = (1u << lane) - 1u;
+            __syncthreads();
 #pragma unroll
-        for (int q = 0; q < ITEMS; ++q) {
-            const uint32_t k = q * TAB_THREADS + threadIdx.x;
-            uint32_t parent = k, cand[CAND];
-            int nc = 0;
-            if (k < n_t) {
-                const uint32_t key = kv[q];
-                const uint32_t W2 = W + 2, centre = tab_pid(pv[q], W);
-                // j: an earlier neighbour within dt
-                auto consider = [&](uint32_t j) {
-                    uint32_t other = j;
-                    if (parent == k) { parent = j; return; }
-                    if (j < parent) { other = parent; parent = j; }
-                    if (nc < CAND) {
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                uint32_t parent = k, cand[CAND];
+                int nc = 0;
+                if (k < n_t) {
+                    tab_walk(S, k, kv[q], tab_pid(pv[q], W), W2, dt, parent, cand, nc);
+                    S.par[k] = parent;
+                }
+                tab_append(S, k, cand, nc, lane);
+            }
+        } else {
+            // band by band: a band's table holds its rows and the rows just
+            // above and below; its hits are listed and walked by all lanes,
+            // then the entries it pushed are cleared for the next band
+            if (threadIdx.x < TAB_MAX_BANDS) S.wl_count[threadIdx.x] = 0;
 #pragma unroll
-                        for (int i = 0; i < CAND; ++i)
-                            if (i == nc) cand[i] = other;
-                        ++nc;
-                    } else {
-                        const uint32_t slot = atomicAdd(&S.nedges, 1u);
-                        if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | other;
+            for (int q = 0; q < ITEMS; ++q) {
+                const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                if (k < n_t) { S.key[k] = kv[q]; S.pix[k] = pv[q]; }
+            }
+            __syncthreads();
+            for (uint32_t b = 0; b < nb; ++b) {
+                const uint32_t y0 = b * rpb, y1 = y0 + rpb < H ? y0 + rpb : H;
+#pragma unroll
+                for (int q = 0; q < ITEMS; ++q) {
+                    const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                    const uint32_t y = pv[q] >> 16;
+                    const bool in = k < n_t && y + 1 >= y0 && y <= y1;   // rows y0 - 1 .. y1
+                    if (in)
+                        S.next[k] = tab_push(S.tab, (y + 1 - y0) * W2 + (pv[q] & 0xFFFFu) + 1, (uint16_t)k);
+                    const bool own = in && y >= y0 && y < y1;
+                    const uint32_t m = __ballot_sync(0xffffffffu, own);
+                    uint32_t slot0 = 0;
+                    if (lane == 0 && m) slot0 = atomicAdd(&S.wl_count[b], (uint32_t)__popc(m));
+                    slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+                    if (own) S.wl[slot0 + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
+                }
+                __syncthreads();
+                const uint32_t cnt = S.wl_count[b];
+                for (uint32_t base = 0; base < cnt; base += TAB_THREADS) {
+                    const uint32_t idx = base + threadIdx.x;
+                    uint32_t k = 0, parent = 0, cand[CAND];
+                    int nc = 0;
+                    if (idx < cnt) {
+                        k = S.wl[idx];
+                        parent = k;
+                        const uint32_t pix = S.pix[k];
+                        tab_walk(S, k, S.key[k], ((pix >> 16) + 1 - y0) * W2 + (pix & 0xFFFFu) + 1, W2, dt,
+                                 parent, cand, nc);
+                        S.par[k] = parent;
                     }
-                };
-                // heads of the 9 lists first (independent loads), then the head
-                // entries without loops or branches around the loads; lists
-                // with a second entry (a pixel hit more than once in the tile:
-                // rare) are walked afterwards
-                uint32_t hd[9];
-#pragma unroll
-                for (int n = 0; n < 9; ++n) hd[n] = S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)];
-                uint32_t more = 0;
-#pragma unroll
-                for (int n = 0; n < 9; ++n) {
-                    const uint32_t j = hd[n];
-                    const uint32_t jm = j & (TILE - 1);   // an empty head reads a harmless entry
-                    const uint32_t kj = S.key[jm], nx = S.next[jm];
-                    const bool has = j != TAB_NONE;
-                    more |= (has && nx != TAB_NONE ? 1u : 0u) << n;
-                    if (has && j < k && key - kj <= dt) consider(j);
+                    tab_append(S, k, cand, nc, lane);
                 }
-                while (more) {   // lists holding more than one hit
-                    const int n = __ffs(more) - 1;
-                    more &= more - 1;
-                    uint32_t j = S.next[S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)]];
-                    int steps = 1;
-                    for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps)
-                        if (j < k && key - S.key[j] <= dt) consider(j);
-                    if (j != TAB_NONE) S.overflow = 1;
-                }
-                S.par[k] = parent;
-            }
-            const uint32_t most = __reduce_max_sync(0xffffffffu, (uint32_t)nc);
+                __syncthreads();
 #pragma unroll
-            for (int c = 0; c < CAND; ++c) {
-                if (c >= (int)most) break;
-                const bool has = c < nc;
-                const uint32_t m = __ballot_sync(0xffffffffu, has);
-                uint32_t slot0 = 0;
-                if (lane == 0) slot0 = atomicAdd(&S.nedges, (uint32_t)__popc(m));
-                slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-                const uint32_t slot = slot0 + __popc(m & lt_mask);
-                if (has && slot < TAB_EDGES) S.edges[slot] = (k << 16) | cand[c];
+                for (int q = 0; q < ITEMS; ++q) {
+                    const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                    const uint32_t y = pv[q] >> 16;
+                    if (k < n_t && y + 1 >= y0 && y <= y1) S.tab[(y + 1 - y0) * W2 + (pv[q] & 0xFFFFu) + 1] = TAB_NONE;
+                }
+                __syncthreads();
             }
         }
         __syncthreads();
@@ -530,10 +609,12 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 const uint32_t slot = atomicAdd(&w.prob->redo_count, 1u);
                 w.redo[slot] = t;
             }
+            if (nb == 1) {   // (banded tables were cleared band by band)
 #pragma unroll
-            for (int q = 0; q < ITEMS; ++q) {
-                const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                if (k < n_t) S.tab[tab_pid(pv[q], W)] = TAB_NONE;
+                for (int q = 0; q < ITEMS; ++q) {
+                    const uint32_t k = q * TAB_THREADS + threadIdx.x;
+                    if (k < n_t) S.tab[tab_pid(pv[q], W)] = TAB_NONE;
+                }
             }
             __syncthreads();
             continue;
@@ -545,7 +626,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 const uint32_t r = tab_root(vpar, k);
                 w.parent[begin + k] = begin + r;
                 if (r == k) init_slot(w, begin + k);
-                S.tab[tab_pid(pv[q], W)] = TAB_NONE;   // reset only what this tile touched
+                if (nb == 1) S.tab[tab_pid(pv[q], W)] = TAB_NONE;   // reset only what this tile touched
             }
         }
         __syncthreads();

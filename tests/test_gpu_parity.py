@@ -258,3 +258,22 @@ def test_labels_async_and_two_context_pipeline():
         with pytest.raises(TpcError) as e:
             c.labels_async(bufs[0].data_ptr(), n, device=False)
         assert e.value.name == "TPC_ERR_STATE"
+
+
+@pytest.mark.parametrize("w,h,seed", [(300, 600, 31), (301, 500, 32), (4000, 200, 33), (1024, 1024, 34)])
+def test_banded_table_sensors(w, h, seed):
+    """Sensors larger than the shared-memory pixel table are linked band by
+    band (rows of the table); clusters crossing band edges, odd widths and
+    thin bands (a wide sensor) must come out exact."""
+    rng = np.random.default_rng(seed)
+    n = 60000
+    hits = random_hits(rng, n, w, h, n // 2)
+    # dense vertical tracks so that many clusters cross band edges
+    ys = np.arange(h)
+    tracks = []
+    for x in rng.integers(1, w - 1, 8):
+        t0 = int(rng.integers(0, n // 2))
+        tracks.append(oracle.make_hits(np.full(h, x), ys, t0 + (ys % 7), rng.integers(1, 30, h)))
+    hits = np.concatenate([hits] + tracks)
+    hits = hits[np.argsort(hits["toa"], kind="stable")]
+    check_against_oracle(hits, w, h, 64)
