@@ -138,6 +138,7 @@ struct VarSpace {
         v.glast = mem.alloc<uint32_t>(positions, e);
         v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
         v.changed = mem.alloc<uint32_t>(1, e);
+        v.work = mem.alloc<uint32_t>(1, e);
         v.prob = mem.alloc<Prob>(1, e);
         if (e != cudaSuccess) {
             mem.release();

@@ -140,6 +140,7 @@ struct VarWork {
     uint32_t *glast;           // (b): per root, last key of its group
     uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
     uint32_t *changed;         // (b): a round merged something
+    uint32_t *work;            // (c): next chunk of the grouped order to sweep
     Prob *prob;                // problem view of the grouping sort
 };
 

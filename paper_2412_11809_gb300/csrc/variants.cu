@@ -60,39 +60,124 @@ __device__ __forceinline__ uint32_t seq_find(uint32_t *par, uint32_t x) {
     return x;
 }
 
-// (c): one thread per component start of the root-grouped order.
-__global__ void __launch_bounds__(128) k_static_sweep(Work w, VarWork v) {
+// (c): one warp per component of the root-grouped order (components are
+// contiguous there, in ToA order).  The sweep is sequential over the
+// component's hits, but each step is warp-wide: for hit i the lanes take the
+// earlier hits within dt (32 at a time, newest first), test adjacency and
+// whether the cluster of that hit is still open (its root, the earliest hit,
+// within dt of i), and every open cluster found is joined under the earliest
+// of their roots, together with i.  Whether a cluster is open does not
+// depend on the joins made for i itself (a join only unites open clusters,
+// and the result is open), so the lanes may test their candidates at once.
+// Components of up to SW_CAP hits are staged in shared memory; larger ones
+// run on the grouped arrays in global memory.  Warps take chunks of SW_CHUNK
+// grouped positions from a counter and sweep every component that starts in
+// their chunk.
+constexpr int SW_WARPS = 8;
+constexpr uint32_t SW_CAP = 512;
+constexpr uint32_t SW_CHUNK = 32;
+
+template <bool STAGED>
+struct SweepView {
+    const uint32_t *sk, *sp;   // staged keys and pixels (STAGED)
+    uint32_t *sc;              // parent per component index (staged or global)
+    const uint32_t *skey, *spix, *gv;
+    uint32_t q;                // first grouped position of the component
+    __device__ uint32_t key(uint32_t i) const { return STAGED ? sk[i] : skey[gv[q + i]]; }
+    __device__ uint32_t pix(uint32_t i) const { return STAGED ? sp[i] : spix[gv[q + i]]; }
+    __device__ uint32_t find(uint32_t x) const {   // path halving
+        volatile uint32_t *c = sc;
+        while (true) {
+            const uint32_t p = c[x];
+            if (p == x) return x;
+            const uint32_t gp = c[p];
+            if (gp == p) return p;
+            c[x] = gp;
+            x = gp;
+        }
+    }
+};
+
+template <bool STAGED>
+__device__ void sweep_component(const SweepView<STAGED> &V, uint32_t n, uint32_t dt, int lane) {
+    for (uint32_t i = lane; i < n; i += 32) V.sc[i] = i;
+    __syncwarp();
+    for (uint32_t i = 1; i < n; ++i) {
+        const uint32_t ki = V.key(i), pi = V.pix(i);
+        uint32_t root = 0xFFFFFFFFu;   // the earliest open root joined so far
+        for (uint32_t base = 0; base < i; base += 32) {
+            const bool valid = base + lane < i;
+            const uint32_t j = valid ? i - 1 - base - lane : 0;
+            const bool in = valid && ki - V.key(j) <= dt;
+            if (!__any_sync(0xffffffffu, in)) break;   // keys only fall further back
+            uint32_t r = 0xFFFFFFFFu;
+            if (in && adjacent_v(pi, V.pix(j))) {
+                const uint32_t rj = V.find(j);
+                if (ki - V.key(rj) <= dt) r = rj;   // that cluster is still open
+            }
+            const uint32_t m = __reduce_min_sync(0xffffffffu, r);
+            __syncwarp();
+            if (m != 0xFFFFFFFFu) {
+                const uint32_t target = m < root ? m : root;
+                if (r != 0xFFFFFFFFu && r != target) V.sc[r] = target;
+                if (lane == 0 && root != 0xFFFFFFFFu && root != target) V.sc[root] = target;
+                root = target;
+            }
+            __syncwarp();
+        }
+        if (lane == 0 && root != 0xFFFFFFFFu) V.sc[i] = root;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(SW_WARPS * 32) k_static_sweep(Work w, VarWork v) {
+    __shared__ uint32_t s_k[SW_WARPS][SW_CAP], s_p[SW_WARPS][SW_CAP], s_c[SW_WARPS][SW_CAP];
     const Prob &P = *w.prob;
-    const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
     const uint32_t sel = v.prob->npasses & 1u;
     const uint32_t *gk = v.k[sel], *gv = v.v[sel];
-    uint32_t *cpar = v.cpar;
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-        const Seg &g = w.seg[w.tile_seg[t]];
-        uint32_t begin, end;
-        tile_range(g, t, begin, end);
-        const uint32_t last = g.off + g.n, dt = g.dt;
-        for (uint32_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
-            if (q != g.off && gk[q] == gk[q - 1]) continue;   // not the first of a component
-            uint32_t qe = q + 1;
-            while (qe < last && gk[qe] == gk[q]) ++qe;
-            for (uint32_t i = q; i < qe; ++i) cpar[i] = i;
-            for (uint32_t i = q + 1; i < qe; ++i) {
-                const uint32_t si = gv[i], ki = skey[si], pi = w.spix[si];
-                for (uint32_t j = i; j-- > q;) {
-                    const uint32_t sj = gv[j];
-                    if (ki - skey[sj] > dt) break;   // older members: clusters closed
-                    if (!adjacent_v(pi, w.spix[sj])) continue;
-                    const uint32_t rj = seq_find(cpar, j);
-                    if (ki - skey[gv[rj]] > dt) continue;   // cluster's first hit too old
-                    const uint32_t ri = seq_find(cpar, i);
-                    if (ri != rj) {   // the earlier root stays root (first ToA)
-                        if (ri < rj) cpar[rj] = ri; else cpar[ri] = rj;
-                    }
-                }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Seg &g = w.seg[0];
+    const uint32_t first = g.off, last = g.off + g.n, dt = g.dt;
+    const uint32_t nchunks = (g.n + SW_CHUNK - 1) / SW_CHUNK;
+    while (true) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(v.work, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const uint32_t q = first + c * SW_CHUNK + lane;
+        uint32_t starts = __ballot_sync(0xffffffffu, q < last && (q == first || gk[q] != gk[q - 1]));
+        while (starts) {
+            const uint32_t q0 = first + c * SW_CHUNK + (__ffs(starts) - 1);
+            starts &= starts - 1;
+            // the component's end: the first grouped position with another root
+            const uint32_t key0 = gk[q0];
+            uint32_t n = 0;
+            for (uint32_t p0 = q0 + 1;; p0 += 32) {
+                const uint32_t p = p0 + lane;
+                const uint32_t stop = __ballot_sync(0xffffffffu, p >= last || gk[p] != key0);
+                if (stop) { n = p0 + (__ffs(stop) - 1) - q0; break; }
             }
-            for (uint32_t i = q; i < qe; ++i) w.parent[gv[i]] = gv[seq_find(cpar, i)];
+            if (n == 1) {
+                if (lane == 0) w.parent[gv[q0]] = gv[q0];
+                continue;
+            }
+            if (n <= SW_CAP) {
+                for (uint32_t i = lane; i < n; i += 32) {
+                    const uint32_t si = gv[q0 + i];
+                    s_k[warp][i] = skey[si];
+                    s_p[warp][i] = w.spix[si];
+                }
+                __syncwarp();
+                const SweepView<true> V{s_k[warp], s_p[warp], s_c[warp], skey, w.spix, gv, q0};
+                sweep_component(V, n, dt, lane);
+                for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
+            } else {
+                const SweepView<false> V{nullptr, nullptr, v.cpar + q0, skey, w.spix, gv, q0};
+                sweep_component(V, n, dt, lane);
+                for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
+            }
+            __syncwarp();   // the staging is rewritten for the next component
         }
     }
 }
@@ -219,7 +304,8 @@ Work variant_view(const Work &w, const VarWork &v) {
 }
 
 void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L) {
-    k_static_sweep<<<L.fit(k_static_sweep, 128, 0), 128, 0, L.stream>>>(w, v);
+    cudaMemsetAsync(v.work, 0, sizeof(uint32_t), L.stream);
+    k_static_sweep<<<L.fit(k_static_sweep, SW_WARPS * 32, 0), SW_WARPS * 32, 0, L.stream>>>(w, v);
     L.mark("k_static_sweep");
 }
 
