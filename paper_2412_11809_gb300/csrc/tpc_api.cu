@@ -137,6 +137,7 @@ struct VarSpace {
         v.cpar = mem.alloc<uint32_t>(positions, e);
         v.glast = mem.alloc<uint32_t>(positions, e);
         v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
+        v.latest = mem.alloc<uint32_t>(9 * positions, e);
         v.changed = mem.alloc<uint32_t>(1, e);
         v.work = mem.alloc<uint32_t>(1, e);
         v.prob = mem.alloc<Prob>(1, e);

@@ -139,6 +139,7 @@ struct VarWork {
     uint32_t *cpar;            // (c): forest over the root-grouped order
     uint32_t *glast;           // (b): per root, last key of its group
     uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
+    uint32_t *latest;          // (b): per position, 9 slots: latest earlier hit on each neighbour pixel
     uint32_t *changed;         // (b): a round merged something
     uint32_t *work;            // (c): next chunk of the grouped order to sweep
     Prob *prob;                // problem view of the grouping sort

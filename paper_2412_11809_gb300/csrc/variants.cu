@@ -221,6 +221,40 @@ __global__ void __launch_bounds__(1024) k_pixel_scan(Work w, VarWork v) {
     }
 }
 
+// (b), once before the rounds: for every hit and each of its 9 pixels the
+// latest earlier hit there (binary search in the pixel's timeline), or none.
+__global__ void __launch_bounds__(256) k_pixel_latest(Work w, VarWork v) {
+    const Prob &P = *w.prob;
+    const uint32_t nt = P.ntiles;
+    const uint32_t *tl = v.v[v.prob->npasses & 1u];   // sorted positions grouped by pixel
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        const uint32_t W = g.width, H = g.height;
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
+            const uint32_t pix = w.spix[s];
+            const int x = (int)(pix & 0xFFFFu), y = (int)(pix >> 16);
+#pragma unroll
+            for (int n = 0; n < 9; ++n) {
+                const int nx = x + n % 3 - 1, ny = y + n / 3 - 1;
+                uint32_t L = 0xFFFFFFFFu;
+                if (nx >= 0 && nx < (int)W && ny >= 0 && ny < (int)H) {
+                    const uint32_t p = (uint32_t)ny * W + (uint32_t)nx;
+                    const uint32_t first = v.pix_start[p];
+                    uint32_t lo = first, hi = v.pix_start[p + 1];   // last entry < s
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (tl[g.off + mid] < s) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo != first) L = tl[g.off + lo - 1];
+                }
+                v.latest[(size_t)s * 9 + n] = L;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_group_last_reset(Work w, VarWork v) {
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
@@ -233,6 +267,8 @@ __global__ void __launch_bounds__(256) k_group_last_reset(Work w, VarWork v) {
     }
 }
 
+// A group's last key: only hits that could raise the stored maximum issue
+// the atomic (a large group would otherwise serialise on one address).
 __global__ void __launch_bounds__(256) k_group_last(Work w, VarWork v) {
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
@@ -241,8 +277,10 @@ __global__ void __launch_bounds__(256) k_group_last(Work w, VarWork v) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
-        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x)
-            atomicMax(&v.glast[gfind(w.parent, s)], skey[s]);
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
+            const uint32_t r = gfind(w.parent, s), k = skey[s];
+            if (*reinterpret_cast<volatile uint32_t *>(&v.glast[r]) < k) atomicMax(&v.glast[r], k);
+        }
     }
 }
 
@@ -251,36 +289,25 @@ __global__ void __launch_bounds__(256) k_global_round(Work w, VarWork v) {
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
-    const uint32_t *tl = v.v[v.prob->npasses & 1u];   // sorted positions grouped by pixel
     bool changed = false;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
-        const uint32_t W = g.width, H = g.height, dt = g.dt;
+        const uint32_t dt = g.dt;
         for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
-            const uint32_t key = skey[s], pix = w.spix[s];
-            const int x = (int)(pix & 0xFFFFu), y = (int)(pix >> 16);
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int ny = y + dy;
-                if (ny < 0 || ny >= (int)H) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int nx = x + dx;
-                    if (nx < 0 || nx >= (int)W) continue;
-                    const uint32_t p = (uint32_t)ny * W + (uint32_t)nx;
-                    uint32_t lo = v.pix_start[p], hi = v.pix_start[p + 1];   // last entry < s
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (tl[g.off + mid] < s) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo == v.pix_start[p]) continue;
-                    const uint32_t L = tl[g.off + lo - 1];
-                    const uint32_t rl = gfind(w.parent, L), rh = gfind(w.parent, s);
-                    if (rl == rh) continue;
-                    if ((uint64_t)key <= (uint64_t)v.glast[rl] + dt) {
-                        gunion(w.parent, s, L);
-                        changed = true;
-                    }
+            const uint32_t key = skey[s];
+            uint32_t rh = gfind(w.parent, s);
+#pragma unroll
+            for (int n = 0; n < 9; ++n) {
+                const uint32_t L = v.latest[(size_t)s * 9 + n];
+                if (L == 0xFFFFFFFFu) continue;
+                const uint32_t rl = gfind(w.parent, L);
+                if (rl == rh) continue;
+                if ((uint64_t)key <= (uint64_t)v.glast[rl] + dt) {
+                    gunion(w.parent, s, L);
+                    rh = gfind(w.parent, s);
+                    changed = true;
                 }
             }
         }
@@ -314,6 +341,8 @@ void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, c
     k_pixel_hist<<<L.fit(k_pixel_hist, 256, 0), 256, 0, L.stream>>>(w, v);
     k_pixel_scan<<<1, 1024, 0, L.stream>>>(w, v);
     L.mark("k_pixel_hist_scan");
+    k_pixel_latest<<<L.fit(k_pixel_latest, 256, 0), 256, 0, L.stream>>>(w, v);
+    L.mark("k_pixel_latest");
 }
 
 void launch_global_round(const Work &w, const VarWork &v, const Launch &L) {
