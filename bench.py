@@ -310,6 +310,37 @@ def run_serving(args, dev, torch):
     return out
 
 
+def run_large_sensor(args, dev, torch):
+    """Timepix4-size sensor (448x512, the 2.5 Ghits/s config-1 mix) at
+    args.large_scale of its 512 Mi hits: variant (a) at dt = 128 and 384
+    ticks, variants (c) and (b) at dt = 128; one flush per step, inputs
+    resident on the device, CUDA events on the context stream."""
+    import synth
+    from paper_2412_11809_gb300 import Clusterer
+    hits, _ = synth.cfg4(scale=args.large_scale, seed=4000)
+    n = len(hits)
+    d = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    out = {"sensor": "448x512", "hits": n}
+    for name, variant, dt, steps in (("local_dt128", "local", 128, 5), ("local_dt384", "local", 384, 5),
+                                     ("static_dt128", "static", 128, 3), ("global_dt128", "global", 128, 2)):
+        c = Clusterer(448, 512, dt, variant=variant, stream=stream)
+        c.push(d)
+        c.flush()
+        c.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            c.push(d)
+            c.flush()
+        e1.record(stream)
+        e1.synchronize()
+        c.sync()
+        out[name] = n * steps / (e0.elapsed_time(e1) / 1e3)
+        c.close()
+    return out
+
+
 def run_batched(args, dev, torch):
     """16 detectors (ten 256x256, six 448x512): one batched step (one CUDA-graph
     replay, persistent CTAs over every detector's tiles) against one flush per
@@ -490,10 +521,11 @@ def run_gpu(args):
                "sample": f"first {n_sample} hits of the same stream, labels + features, "
                          f"single-threaded on a host with {cpu_cores()} cores"}
 
-    serving = batched = None
+    serving = batched = large = None
     if rank == 0 and not args.no_extras:
         batched = run_batched(args, dev, torch)
         serving = run_serving(args, dev, torch)
+        large = run_large_sensor(args, dev, torch)
 
     if rank == 0:
         line = {
@@ -521,6 +553,7 @@ def run_gpu(args):
             "clocks": clocks.summary(),
             "serving": serving,
             "batched": batched,
+            "large_sensor": large,
         }
         print(json.dumps(line), flush=True)
     c.close()
@@ -543,6 +576,8 @@ def main():
     ap.add_argument("--serving-hits", type=int, default=4 * 2**20, help="base hits per serving stream")
     ap.add_argument("--serving-chunks", type=int, default=1024)
     ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--large-scale", type=float, default=0.125,
+                    help="fraction of the 512 Mi-hit 448x512 stream for the large-sensor lines")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
