@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
 __device__ __forceinline__ bool cluster_closed(const Seg &g, uint32_t maxkey) {
     if (g.close_mode == CLOSE_ALL) return true;
     if (g.close_mode == CLOSE_NONE) return false;
-    return g.toa_min + (uint64_t)maxkey <= g.watermark;
+    return g.key_base + (uint64_t)maxkey <= g.watermark;
 }
 
 __global__ void __launch_bounds__(256) k_labels(Work w) {
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(TILE_WORDS) k_records(Work w) {
                 const Slot sl = w.slot[r];
                 rec.size = (int64_t)sl.size;
                 rec.sum_tot = (int64_t)sl.tot;
-                rec.first_toa = g.toa_min + skey[r];
+                rec.first_toa = g.key_base + skey[r];
                 // fp32 quotient of the exact integer sums: three roundings, each
                 // at most 2^-24 relative (FP64 is a slow pipe on this GPU)
                 const float sw = (float)sl.tot;

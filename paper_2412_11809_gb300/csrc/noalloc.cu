@@ -175,9 +175,8 @@ extern "C" int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width,
     const Launch L{sms * 4, st, nullptr, sms};
     k_na_begin<<<1, 1, 0, st>>>(w, s, NA_TILES, NA_POS);
     launch_setup(w, 1, L);
-    launch_prepare(w, L);
-    launch_seg_finalize(w, L);
     launch_sort_fast(w, L);
+    launch_seg_finalize(w, L);
     launch_make_keys(w, L);
     for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
     launch_gather(w, L);

@@ -1,6 +1,6 @@
-// Step set-up, coalesced 16-byte hit loads with range validation and ToA
-// min/max (Algorithm 3, steps 1-2: the hits arrive on the device), sort keys,
-// and the post-sort gather of pixel coordinates.
+// Step set-up (Algorithm 3, steps 1-2: the hits arrive on the device), the
+// per-segment decisions taken once the tile sort has seen every hit, and the
+// general sort's keys and post-sort gather of pixel coordinates.
 #include "tpc_internal.cuh"
 
 namespace tpc {
@@ -66,84 +66,20 @@ __global__ void k_setup(Work w, int nsegs) {
     }
 }
 
-__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
-    for (int o = 16; o; o >>= 1) {
-        uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
-        v = u < v ? u : v;
-    }
-    return v;
-}
-__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
-    for (int o = 16; o; o >>= 1) {
-        uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
-        v = u > v ? u : v;
-    }
-    return v;
-}
-
-// Load every hit once (16-byte vector loads, consecutive threads on
-// consecutive hits), reject hits outside the sensor, reduce ToA min/max.
-__global__ void __launch_bounds__(256) k_prepare(Work w) {
-    __shared__ uint64_t s_red[3][8];
-    const uint32_t nt = w.prob->ntiles;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-        const uint32_t si = w.tile_seg[t];
-        const Seg &g = w.seg[si];
-        uint32_t begin, end;
-        tile_range(g, t, begin, end);
-        const tpc_hit *hits = g.hits;
-        const uint32_t off = g.off, W = g.width, H = g.height, nc = g.n_carry;
-        uint64_t mn = ~0ull, mx = 0, cmn = ~0ull;
-        bool bad = false;
-        constexpr int U = 4;
-        for (uint32_t p0 = begin + threadIdx.x; p0 < end; p0 += U * blockDim.x) {
-            uint4 v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t pos = p0 + u * blockDim.x;
-                if (pos < end) v[u] = ld_hit(hits + (pos - off));
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t pos = p0 + u * blockDim.x;
-                if (pos >= end) continue;
-                const uint32_t j = pos - off;
-                bad |= hit_x(v[u]) >= W || hit_y(v[u]) >= H;
-                const uint64_t toa = hit_toa(v[u]);
-                mn = toa < mn ? toa : mn;
-                mx = toa > mx ? toa : mx;
-                if (j >= nc) cmn = toa < cmn ? toa : cmn;
-            }
-        }
-        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&w.prob->err, E_RANGE);
-        mn = warp_min_u64(mn);
-        mx = warp_max_u64(mx);
-        cmn = warp_min_u64(cmn);
-        if (lane == 0) { s_red[0][warp] = mn; s_red[1][warp] = mx; s_red[2][warp] = cmn; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-                mn = s_red[0][i] < mn ? s_red[0][i] : mn;
-                mx = s_red[1][i] > mx ? s_red[1][i] : mx;
-                cmn = s_red[2][i] < cmn ? s_red[2][i] : cmn;
-            }
-            Seg &gw = w.seg[si];
-            atomicMin(reinterpret_cast<unsigned long long *>(&gw.toa_min), (unsigned long long)mn);
-            atomicMax(reinterpret_cast<unsigned long long *>(&gw.toa_max), (unsigned long long)mx);
-            atomicMin(reinterpret_cast<unsigned long long *>(&gw.chunk_min), (unsigned long long)cmn);
-        }
-        __syncthreads();
-    }
-}
-
-// One CTA: per-segment radix pass count, ToA span check, and the streaming
+// One CTA, after the tile sort, merge and check: per-segment radix pass
+// count, the ToA span check, the choice of sort (the tile sort's keys are
+// relative to fast_key_base; if a ToA lies outside 2^32 ticks of that base,
+// or the check found the tiles out of order, every segment takes the
+// general sort with keys relative to its minimum ToA) and the streaming
 // watermark.  A later hit j satisfies toa_j > seen_max - max_disorder (the
 // t-ordered property, Section 3.1), and can join hit i only if
 // toa_j - toa_i <= dt, so every cluster whose last ToA <=
 // seen_max - max_disorder - dt is final.
 __global__ void k_seg_finalize(Work w) {
+    __shared__ uint32_t s_fallback;
     const uint32_t nsegs = w.prob->nsegs;
+    if (threadIdx.x == 0) s_fallback = w.prob->fallback;
+    __syncthreads();
     for (uint32_t s = threadIdx.x; s < nsegs; s += blockDim.x) {
         Seg &g = w.seg[s];
         uint32_t passes = 0;
@@ -155,9 +91,11 @@ __global__ void k_seg_finalize(Work w) {
                 uint32_t bits = 64 - __clzll((long long)span);
                 passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
             }
+            const uint64_t fb = fast_key_base(g);
+            if (g.toa_min < fb || g.toa_max - fb > 0xFFFFFFFFull) atomicOr(&s_fallback, 1u);
         }
         g.npasses = passes;
-        atomicMax(&w.prob->lsd_passes, passes);   // used only if the fast sort falls back
+        atomicMax(&w.prob->lsd_passes, passes);   // used only by the general sort
         if (!g.ss) {
             g.close_mode = CLOSE_ALL;   // one-shot: the end of the stream
             continue;
@@ -179,6 +117,16 @@ __global__ void k_seg_finalize(Work w) {
         } else {
             g.close_mode = CLOSE_NONE;
         }
+    }
+    __syncthreads();
+    const uint32_t fallback = s_fallback;
+    for (uint32_t s = threadIdx.x; s < nsegs; s += blockDim.x) {
+        Seg &g = w.seg[s];
+        g.key_base = fallback || !g.n ? g.toa_min : fast_key_base(g);
+    }
+    if (threadIdx.x == 0 && fallback) {
+        w.prob->fallback = 1u;
+        w.prob->npasses = w.prob->lsd_passes;
     }
 }
 
@@ -247,10 +195,6 @@ __global__ void __launch_bounds__(256) k_gather(Work w) {
 void launch_setup(const Work &w, int nsegs, const Launch &L) {
     k_setup<<<1, 1024, 0, L.stream>>>(w, nsegs);
     L.mark("k_setup");
-}
-void launch_prepare(const Work &w, const Launch &L) {
-    k_prepare<<<L.fit(k_prepare, 256, 0), 256, 0, L.stream>>>(w);
-    L.mark("k_prepare");
 }
 void launch_seg_finalize(const Work &w, const Launch &L) {
     k_seg_finalize<<<1, 256, 0, L.stream>>>(w);

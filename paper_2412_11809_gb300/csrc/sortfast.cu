@@ -55,16 +55,19 @@ struct LsShared {
     uint16_t dstart[LS_RADIX];
     uint32_t warp[32];
     uint32_t kmin[LS_WARPS], kmax[LS_WARPS];
+    unsigned long long tmin[LS_WARPS], tmax[LS_WARPS], cmin[LS_WARPS];
 };
 
 constexpr int LS_SMEM = (int)sizeof(LsShared);
 
-// Only keys and the permutation live in shared memory (four CTAs fit an SM,
-// as the registers allow); pixels and ToTs are fetched again at output, in
-// sorted order, from the tile just read (still in L2).  Per pass a thread
+// Only keys and the permutation live in shared memory; pixels and ToTs are
+// fetched again at output, in sorted order, from the tile just read (still in
+// L2), where the pixels are also checked against the sensor.  The load phase
+// also reduces the segment's ToA extremes (this pass is the first to see
+// every hit).  Per pass a thread
 // holds its 16 elements' local indices two to a register and each digit
 // with its rank among the warp's equal digits in one register.
-__global__ void __launch_bounds__(LS_THREADS, 4) k_tile_sort(Work w) {
+__global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
     extern __shared__ __align__(16) unsigned char ls_raw[];
     LsShared &S = *reinterpret_cast<LsShared *>(ls_raw);
     const Prob &P = *w.prob;
@@ -77,8 +80,10 @@ __global__ void __launch_bounds__(LS_THREADS, 4) k_tile_sort(Work w) {
         tile_range(g, t, begin, end);
         const uint32_t n_t = end - begin;
         const tpc_hit *hits = g.hits + (begin - g.off);
-        const uint64_t base = g.toa_min;
+        const uint64_t base = fast_key_base(g);
+        const uint32_t new0 = g.n_carry > begin - g.off ? g.n_carry - (begin - g.off) : 0;   // first new hit
         uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
+        uint64_t tmin = ~0ull, tmax = 0, cmin = ~0ull;   // ToA extremes; minimum of the new hits
         constexpr int HALF = LS_ITEMS / 2;   // two batches of loads keep registers in bounds
 #pragma unroll
         for (int hb = 0; hb < 2; ++hb) {
@@ -92,7 +97,11 @@ __global__ void __launch_bounds__(LS_THREADS, 4) k_tile_sort(Work w) {
             for (int r = 0; r < HALF; ++r) {
                 const uint32_t li = (hb * HALF + r) * LS_THREADS + threadIdx.x;
                 if (li < n_t) {
-                    const uint32_t key = (uint32_t)((((uint64_t)tv[r].y << 32) | tv[r].x) - base);
+                    const uint64_t toa = ((uint64_t)tv[r].y << 32) | tv[r].x;
+                    const uint32_t key = (uint32_t)(toa - base);
+                    tmin = toa < tmin ? toa : tmin;
+                    tmax = toa > tmax ? toa : tmax;
+                    if (li >= new0) cmin = toa < cmin ? toa : cmin;
                     S.key[li] = key;
                     S.idx[li] = (uint16_t)li;
                     kmin = key < kmin ? key : kmin;
@@ -106,9 +115,29 @@ __global__ void __launch_bounds__(LS_THREADS, 4) k_tile_sort(Work w) {
             kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
             kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
         }
-        if (lane == 0) { S.kmin[warp] = kmin; S.kmax[warp] = kmax; }
+        tmin = warp_min_u64(tmin);
+        tmax = warp_max_u64(tmax);
+        cmin = warp_min_u64(cmin);
+        if (lane == 0) {
+            S.kmin[warp] = kmin;
+            S.kmax[warp] = kmax;
+            S.tmin[warp] = tmin;
+            S.tmax[warp] = tmax;
+            S.cmin[warp] = cmin;
+        }
         __syncthreads();
         for (int q = 0; q < LS_WARPS; ++q) { kmin = min(kmin, S.kmin[q]); kmax = max(kmax, S.kmax[q]); }
+        if (threadIdx.x == 0) {   // the segment's ToA extremes (Algorithm 3, step 2)
+            for (int q = 1; q < LS_WARPS; ++q) {
+                tmin = S.tmin[q] < tmin ? S.tmin[q] : tmin;
+                tmax = S.tmax[q] > tmax ? S.tmax[q] : tmax;
+                cmin = S.cmin[q] < cmin ? S.cmin[q] : cmin;
+            }
+            Seg &gw = w.seg[w.tile_seg[t]];
+            atomicMin(reinterpret_cast<unsigned long long *>(&gw.toa_min), (unsigned long long)tmin);
+            atomicMax(reinterpret_cast<unsigned long long *>(&gw.toa_max), (unsigned long long)tmax);
+            atomicMin(reinterpret_cast<unsigned long long *>(&gw.chunk_min), (unsigned long long)cmin);
+        }
         const uint32_t span = kmax - kmin;
         const int passes = span ? (32 - __clz(span) + LS_BITS - 1) / LS_BITS : 0;
 
@@ -176,15 +205,17 @@ __global__ void __launch_bounds__(LS_THREADS, 4) k_tile_sort(Work w) {
             }
             __syncthreads();
         }
+        bool bad = false;   // a hit outside the sensor
         for (uint32_t j = threadIdx.x; j < n_t; j += LS_THREADS) {
             const uint32_t li = S.idx[j];
             const uint2 px = __ldg(reinterpret_cast<const uint2 *>(hits + li));   // x | y << 16, ToT
+            bad |= (px.x & 0xFFFFu) >= g.width || (px.x >> 16) >= g.height;
             w.keys[0][begin + j] = S.key[li];
             w.vals[0][begin + j] = begin + li;
             w.spix[begin + j] = clamp_pix(px.x, g.width, g.height);
             w.stot[begin + j] = (uint16_t)(px.y & 0xFFFFu);
         }
-        __syncthreads();
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&w.prob->err, E_RANGE);
     }
 }
 
@@ -312,10 +343,7 @@ __global__ void __launch_bounds__(256) k_sort_check(Work w) {
         const uint32_t ka = w.keys[0][s], kb = w.keys[0][s + 1];
         bad |= ka > kb || (ka == kb && w.vals[0][s] > w.vals[0][s + 1]);
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) {
-        w.prob->fallback = 1u;
-        w.prob->npasses = w.prob->lsd_passes;
-    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) w.prob->fallback = 1u;
 }
 
 cudaError_t init_sortfast_attributes() {

@@ -300,9 +300,8 @@ cudaError_t upload_segs(tpc_ctx *c, const Work &w, const Seg *segs, int nsegs, c
 
 void enqueue_kernels(const Work &w, int nsegs, const Launch &L) {
     launch_setup(w, nsegs, L);
-    launch_prepare(w, L);
-    launch_seg_finalize(w, L);
     launch_sort_fast(w, L);
+    launch_seg_finalize(w, L);
     launch_make_keys(w, L);
     for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
     launch_gather(w, L);
@@ -642,9 +641,8 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
     const Launch L{grid_of(c), c->stream, tr, c->sms, c->ctas_per_sm};
     if (tr) cudaEventRecord(tr->ev[0], c->stream);
     launch_setup(w, 1, L);
-    launch_prepare(w, L);
-    launch_seg_finalize(w, L);
     launch_sort_fast(w, L);
+    launch_seg_finalize(w, L);
     launch_make_keys(w, L);
     for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
     launch_gather(w, L);

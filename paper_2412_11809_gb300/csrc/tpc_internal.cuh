@@ -75,6 +75,7 @@ struct Seg {
     uint32_t tile0, ntiles;
     uint32_t npasses;          // radix passes this segment needs
     uint64_t toa_min, toa_max;
+    uint64_t key_base;         // sort keys are ToA - key_base (32 bits)
     uint64_t chunk_min;        // min ToA of the new hits
     uint64_t watermark;        // CLOSE_WM: close clusters whose last ToA <= watermark
     uint64_t seen_after;       // streaming: max ToA seen after this step
@@ -230,9 +231,33 @@ __device__ __forceinline__ uint32_t hit_y(uint4 v) { return v.x >> 16; }
 __device__ __forceinline__ uint32_t hit_tot(uint4 v) { return v.y & 0xFFFFu; }
 __device__ __forceinline__ uint64_t hit_toa(uint4 v) { return ((uint64_t)v.w << 32) | v.z; }
 
-// Pixel clamped into the sensor.  k_prepare reports hits outside it (E_RANGE)
-// but the step still runs to its end, and the link kernels index per-pixel
-// tables with the sorted pixels, so the sorts store them clamped.
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+    for (int o = 16; o; o >>= 1) {
+        uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+    for (int o = 16; o; o >>= 1) {
+        uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
+// Key base of the tile sort, known before any pass over the hits: 2^31 ticks
+// before the segment's first hit.  Its keys are exact when every ToA lies
+// within 2^31 ticks of that hit (checked once the extremes are known; the
+// general sort, with base = minimum ToA, takes over otherwise).
+__device__ __forceinline__ uint64_t fast_key_base(const Seg &g) {
+    const uint64_t t0 = g.n ? hit_toa(ld_hit(g.hits)) : 0;
+    return t0 > (1ull << 31) ? t0 - (1ull << 31) : 0;
+}
+
+// Pixel clamped into the sensor.  The tile sort reports hits outside it
+// (E_RANGE) but the step still runs to its end, and the link kernels index
+// per-pixel tables with the sorted pixels, so the sorts store them clamped.
 __device__ __forceinline__ uint32_t clamp_pix(uint32_t pix, uint32_t W, uint32_t H) {
     uint32_t x = pix & 0xFFFFu, y = pix >> 16;
     x = x < W ? x : W - 1;
@@ -283,7 +308,6 @@ struct Launch {
 
 cudaError_t init_kernel_attributes();   // once per process and device, before capture
 void launch_setup(const Work &w, int nsegs, const Launch &L);
-void launch_prepare(const Work &w, const Launch &L);
 void launch_seg_finalize(const Work &w, const Launch &L);
 void launch_make_keys(const Work &w, const Launch &L);
 void launch_sort_fast(const Work &w, const Launch &L);

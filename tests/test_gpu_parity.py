@@ -277,3 +277,14 @@ def test_banded_table_sensors(w, h, seed):
     hits = np.concatenate([hits] + tracks)
     hits = hits[np.argsort(hits["toa"], kind="stable")]
     check_against_oracle(hits, w, h, 64)
+
+
+def test_wide_span_takes_general_sort():
+    """A step whose ToA span reaches past 2^31 ticks from its first hit (but
+    stays under 2^32) leaves the tile sort's keys out of range; the general
+    sort takes over and the result is still exact."""
+    rng = np.random.default_rng(5)
+    hits = random_hits(rng, 20000, 64, 64, 3_500_000_000)
+    hits = hits[np.argsort(hits["toa"], kind="stable")]
+    lab, _ = check_against_oracle(hits, 64, 64, 200_000_000)
+    assert len(np.unique(lab)) < len(hits)   # clusters did form
