@@ -46,9 +46,8 @@ HIT_DTYPE_NP = np.dtype([("x", "<u2"), ("y", "<u2"), ("tot", "<u2"), ("reserved"
 # (records 16 B, keys/positions/pixels/parents 4 B, labels 8 B); the cluster
 # record bytes are charged per cluster.  Used for the dominant kernel's roofline.
 KERNEL_BYTES_PER_HIT = {
-    # load + validate: the 16-byte record
-    "k_prepare": 16,
-    # in-tile sort: read the record; write key, position, pixel (4 each), ToT (2)
+    # in-tile sort (also the load, range check and ToA extremes): read the
+    # record; write key, position, pixel (4 each), ToT (2)
     "k_tile_sort": 16 + 14,
     # table link: read key and pixel, write the parent
     "k_tile_link_table": 4 + 4 + 4,
