@@ -24,6 +24,7 @@ __global__ void k_setup(Work w, int nsegs) {
                 g.carry_gidx = nullptr;
             }
             g.n = g.n_carry + g.n_new;
+            g.fast_base = fast_key_base(g);
             g.off = off;
             g.tile0 = tile;
             g.ntiles = (g.n + TILE - 1) / TILE;
@@ -91,7 +92,7 @@ __global__ void k_seg_finalize(Work w) {
                 uint32_t bits = 64 - __clzll((long long)span);
                 passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
             }
-            const uint64_t fb = fast_key_base(g);
+            const uint64_t fb = g.fast_base;
             if (g.toa_min < fb || g.toa_max - fb > 0xFFFFFFFFull) atomicOr(&s_fallback, 1u);
         }
         g.npasses = passes;
@@ -122,7 +123,7 @@ __global__ void k_seg_finalize(Work w) {
     const uint32_t fallback = s_fallback;
     for (uint32_t s = threadIdx.x; s < nsegs; s += blockDim.x) {
         Seg &g = w.seg[s];
-        g.key_base = fallback || !g.n ? g.toa_min : fast_key_base(g);
+        g.key_base = fallback || !g.n ? g.toa_min : g.fast_base;
     }
     if (threadIdx.x == 0 && fallback) {
         w.prob->fallback = 1u;

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
         tile_range(g, t, begin, end);
         const uint32_t n_t = end - begin;
         const tpc_hit *hits = g.hits + (begin - g.off);
-        const uint64_t base = fast_key_base(g);
+        const uint64_t base = g.fast_base;
         const uint32_t new0 = g.n_carry > begin - g.off ? g.n_carry - (begin - g.off) : 0;   // first new hit
         uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
         uint64_t tmin = ~0ull, tmax = 0, cmin = ~0ull;   // ToA extremes; minimum of the new hits
@@ -206,13 +206,14 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
             __syncthreads();
         }
         bool bad = false;   // a hit outside the sensor
+        const uint32_t W = g.width, H = g.height;
         for (uint32_t j = threadIdx.x; j < n_t; j += LS_THREADS) {
             const uint32_t li = S.idx[j];
             const uint2 px = __ldg(reinterpret_cast<const uint2 *>(hits + li));   // x | y << 16, ToT
-            bad |= (px.x & 0xFFFFu) >= g.width || (px.x >> 16) >= g.height;
+            bad |= (px.x & 0xFFFFu) >= W || (px.x >> 16) >= H;
             w.keys[0][begin + j] = S.key[li];
             w.vals[0][begin + j] = begin + li;
-            w.spix[begin + j] = clamp_pix(px.x, g.width, g.height);
+            w.spix[begin + j] = clamp_pix(px.x, W, H);
             w.stot[begin + j] = (uint16_t)(px.y & 0xFFFFu);
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&w.prob->err, E_RANGE);

@@ -76,6 +76,7 @@ struct Seg {
     uint32_t npasses;          // radix passes this segment needs
     uint64_t toa_min, toa_max;
     uint64_t key_base;         // sort keys are ToA - key_base (32 bits)
+    uint64_t fast_base;        // the tile sort's key base (fast_key_base, set by k_setup)
     uint64_t chunk_min;        // min ToA of the new hits
     uint64_t watermark;        // CLOSE_WM: close clusters whose last ToA <= watermark
     uint64_t seen_after;       // streaming: max ToA seen after this step
