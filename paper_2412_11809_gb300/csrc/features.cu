@@ -19,7 +19,7 @@
 namespace tpc {
 
 constexpr int ACC_THREADS = 512;
-constexpr int ACC_SPAN = 2048;                    // sorted positions per pass
+constexpr int ACC_SPAN = 1024;                    // sorted positions per pass (measured best)
 constexpr int ACC_ITEMS = ACC_SPAN / ACC_THREADS;
 constexpr int ACC_SMEM = 2 * ACC_SPAN * (int)sizeof(uint32_t) + 3 * ACC_SPAN * (int)sizeof(unsigned long long);
 
@@ -36,7 +36,7 @@ constexpr int ACC_SMEM = 2 * ACC_SPAN * (int)sizeof(uint32_t) + 3 * ACC_SPAN * (
 // shared-memory counter (size << 32 | sum ToT: a span holds at most ACC_SPAN
 // hits of ToT < 2^16, so neither part overflows), and the last key is kept
 // only when a streaming watermark needs it.
-__global__ void __launch_bounds__(ACC_THREADS, 3) k_accumulate(Work w) {
+__global__ void __launch_bounds__(ACC_THREADS, 4) k_accumulate(Work w) {
     extern __shared__ __align__(16) unsigned char acc_raw[];
     unsigned long long *a_wx = reinterpret_cast<unsigned long long *>(acc_raw);
     unsigned long long *a_wy = a_wx + ACC_SPAN, *a_st = a_wy + ACC_SPAN;
