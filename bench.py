@@ -181,6 +181,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows), "sampled": where}
 
 
+def job_rate(ms_local: float, hits_per_rank: int, steps: int, world: int, dist=None, device="cpu"):
+    """Whole-job throughput of a replicated run: the slowest rank's time (max
+    over ranks, all_reduce on `device`) for steps x hits_per_rank on every
+    rank.  Returns (max ms, hits/s over all ranks)."""
+    import torch
+    t = torch.tensor([float(ms_local)], device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, hits_per_rank * world * steps / (ms_max / 1e3)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -429,12 +441,7 @@ def run_gpu(args):
         end.synchronize()
         clocks.mark(t_host0, time.time())
     barrier()
-    ms = start.elapsed_time(end)
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = n * world * args.steps / (ms_max / 1e3)
+    ms_max, value = job_rate(start.elapsed_time(end), n, args.steps, world, dist, dev)
 
     # per-kernel device times (kernels launched one by one, same workload)
     prof = {}
@@ -495,10 +502,7 @@ def run_gpu(args):
     ea.synchronize()
     eb.synchronize()
     barrier()
-    te = torch.tensor([max(e0.elapsed_time(ea), e0.elapsed_time(eb))], device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = n * world * e2e_steps / (float(te.item()) / 1e3)
+    _, e2e_value = job_rate(max(e0.elapsed_time(ea), e0.elapsed_time(eb)), n, e2e_steps, world, dist, dev)
     ctxs[1].close()
 
     # the link itself: one pinned H2D of the step's input, one D2H of its labels

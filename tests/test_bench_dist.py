@@ -1,0 +1,64 @@
+"""The multi-process side of bench.py on CPU (gloo, world size 2): ranks
+agree on the slowest rank's time and the whole-job rate counts every rank's
+hits; the reference arm runs on rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms_local = 10.0 * (rank + 1)   # rank 1 is the slower one
+        q.put((rank, bench.job_rate(ms_local, hits_per_rank=1000, steps=5, world=world, dist=dist)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_job_rate_takes_the_slowest_rank_over_gloo():
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank in (0, 1):
+        ms_max, rate = got[rank]
+        assert ms_max == 20.0
+        assert rate == pytest.approx(1000 * 2 * 5 / 0.020)
+
+
+def test_job_rate_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    ms_max, rate = bench.job_rate(4.0, hits_per_rank=100, steps=2, world=1)
+    assert ms_max == 4.0 and rate == pytest.approx(100 * 2 / 0.004)
+
+
+def test_reference_arm_is_rank0_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0
+    assert out.stdout.strip() == ""
