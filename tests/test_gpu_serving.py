@@ -175,3 +175,18 @@ def test_batched_repeat_and_mixed_sizes():
         for c, (w, h, hits, _, _) in zip(ctxs, dets):
             np.testing.assert_array_equal(c.labels(), oracle.labels(hits, w, h, 128))
             c.close()
+
+
+def test_streaming_large_sensor_banded():
+    """Streaming on a sensor larger than the shared-memory pixel table (linked
+    band by band), chunks cut at arbitrary points."""
+    hits, t = synth.cfg4(scale=600_000 / (512 * 2**20), seed=45)
+    rng = np.random.default_rng(1)
+    sizes, left = [], len(hits)
+    while left:
+        s = int(min(left, rng.integers(5_000, 120_000)))
+        sizes.append(s)
+        left -= s
+    with Clusterer(448, 512, 128, max_disorder=t) as c:
+        idx, lab, rec = collect_stream(c, hits, sizes)
+    check_stream_result(hits, idx, lab, rec, w=448, h=512, dt=128)
