@@ -7,27 +7,30 @@
 // time window and joins every adjacent hit in it (the complete edge set, so
 // the components are exact by construction).
 //
-// k_tile_link: one CTA per tile of TILE ranks, staged in shared memory.
+// k_tile_link_table (the main path): one CTA per tile of TILE ranks with a
+//   per-pixel list table in shared memory (the paper's pixel matrix), for
+//   sensors the table covers in at most TAB_MAX_BANDS bands of rows; see the
+//   comment above the kernel.
+// k_tile_link (sensors the table cannot cover, and tiles the table kernel
+//   gave back): the tile staged in shared memory, then
 //   window mode (sparse tiles: few hits within dt of a hit, on average):
 //     every pair (k, j < k) within dt is checked for adjacency, the pairs
-//     spread evenly over the threads by a prefix sum of the window lengths.
+//     spread evenly over the threads by a prefix sum of the window lengths;
 //   bucket mode (dense tiles): the tile is counting-sorted into buckets of
-//     4x4-pixel cells (hashed onto NBUCKETS buckets) — the role of the
-//     paper's per-pixel reference matrix (Algorithm 3 step 4), sized to the
-//     tile instead of the sensor — and hit k scans the (at most four) buckets
-//     covering its 3x3 neighbourhood.
+//     4x4-pixel cells (hashed onto NBUCKETS buckets) and hit k scans the (at
+//     most four) buckets covering its 3x3 neighbourhood.
 //   Unions run on a shared-memory forest; the smallest rank of each
 //   component (its earliest hit) becomes the tile root in the global forest.
 //
-// k_border_link: edges whose earlier end lies before the tile (the paper's
-// step 5, "border hits at the start of the next chunk").  The halo is every
-// earlier hit within dt of the tile's first hit; the front is every tile hit
-// within dt of the halo's last hit.  Small borders are scanned pairwise
-// (ToA-ordered, stopping at dt); large ones bucket the halo by cell in shared
-// memory, in batches.  Unions run on the global forest.
+// k_border_fast / k_border_link: edges whose earlier end lies before the tile
+// (the paper's step 5, "border hits at the start of the next chunk").  The
+// halo is every earlier hit within dt of the tile's first hit; the front is
+// every tile hit within dt of the halo's last hit.  One warp per border from
+// staged windows when both are small; otherwise block-wide, pairwise or with
+// the halo bucketed by cell.  Unions run on the global forest.
 //
-// k_flatten: full path compression; records each position's root and
-// initialises the per-root feature slots.
+// k_flatten (variants (b) and (c) only): full path compression; records each
+// position's root and initialises the per-root feature slots.
 #include "tpc_internal.cuh"
 
 namespace tpc {

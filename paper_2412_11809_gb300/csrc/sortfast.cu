@@ -2,23 +2,27 @@
 // t late), in three kernels, with the general LSD radix sort (radix.cu) as
 // the fallback:
 //
-//   k_tile_sort   every tile of TILE input positions is loaded once (16-byte
-//                 vector loads) and sorted in shared memory by a block radix
-//                 sort over the key bits that vary inside the tile; the
-//                 sorted keys, positions, pixels and ToTs are written out, so
-//                 no separate gather is needed.
+//   k_tile_sort   every tile of TILE input positions is read (ToA words
+//                 first, pixels and ToTs again at output from L2) and sorted
+//                 in shared memory by a block radix sort over the key bits
+//                 that vary inside the tile; the sorted keys, positions,
+//                 pixels and ToTs are written out, so no separate gather is
+//                 needed.  Being the first pass over the hits, it also
+//                 reduces the segment's ToA extremes and checks the pixels
+//                 against the sensor (Algorithm 3, steps 1-2).
 //   k_tile_merge  the second half of tile t-1 and the first half of tile t
-//                 are merged (merge path).  If every hit lies less than TILE/2
-//                 positions from its place in (ToA, position) order, this
-//                 completes the sort: after the first kernel, the prefix
-//                 ending in the middle of any tile holds exactly the hits that
-//                 belong there, so the windows straddling tile borders only
-//                 need their own contents ordered.
+//                 are merged.  If every hit lies less than TILE/2 positions
+//                 from its place in (ToA, position) order, this completes the
+//                 sort: after the first kernel, the prefix ending in the
+//                 middle of any tile holds exactly the hits that belong
+//                 there, so the windows straddling tile borders only need
+//                 their own contents ordered.
 //   k_sort_check  compares the neighbours at every window border; on any
-//                 inversion the problem is marked for the fallback, whose
-//                 kernels (make_keys, radix passes, gather) otherwise return
-//                 at once.  The result is therefore exact for any input
-//                 order.
+//                 inversion the step is marked for the fallback (k_seg_finalize
+//                 also sends it there when a ToA lies outside the tile sort's
+//                 key range), whose kernels (make_keys, radix passes, gather)
+//                 otherwise return at once.  The result is therefore exact
+//                 for any input order.
 #include "tpc_internal.cuh"
 
 namespace tpc {
