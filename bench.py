@@ -460,50 +460,54 @@ def run_gpu(args):
     b_alg = path_bytes_per_hit(n, n_clusters)
     path_gbs = value / world * b_alg / 1e9
 
-    # end to end: pinned host input, host results, through the same API.  Two
-    # contexts on two CUDA streams take the steps in turn, so one step's copies
-    # overlap the other's kernels: a step's input copy, kernels and label copy
-    # are queued without waiting (tpc_labels_async), and its records are
-    # fetched after the next step is queued (fetching them returns their
-    # count, which waits for that step).
+    # end to end: pinned host input, host results, through the same API.
+    # NCTX contexts on their own CUDA streams take the steps in turn, so
+    # copies in both directions overlap other steps' kernels: a step's input
+    # copy, kernels and label copy are queued without waiting
+    # (tpc_labels_async), and its records are fetched NCTX - 1 steps later
+    # (fetching them returns their count, which waits for that step).
+    NCTX = 3
     pin_in = host_u8.pin_memory()
-    stream2 = torch.cuda.Stream(device=dev)
-    ctxs = [c, Clusterer(W, H, DT, stream=stream2)]
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(NCTX - 1)]
+    ctxs = [c] + [Clusterer(W, H, DT, stream=st) for st in streams[1:]]
     pin_lab = [torch.empty(n, dtype=torch.int64).pin_memory() for _ in ctxs]
-    pin_rec = [torch.empty((n, CLUSTER_DTYPE.itemsize), dtype=torch.uint8).pin_memory() for _ in ctxs]
+    rec_cap = max(1, n // 4)   # cluster records (about 5 % of the hits here)
+    pin_rec = [torch.empty((rec_cap, CLUSTER_DTYPE.itemsize), dtype=torch.uint8).pin_memory() for _ in ctxs]
 
     def issue(k):   # nothing here waits for the device
-        cx = ctxs[k % 2]
+        cx = ctxs[k % NCTX]
         cx.push_ptr(pin_in.data_ptr(), n, device=False)
         cx.flush()
-        cx.labels_async(pin_lab[k % 2].data_ptr(), n, device=False)
+        cx.labels_async(pin_lab[k % NCTX].data_ptr(), n, device=False)
 
     def finish(k):
-        return ctxs[k % 2].features_into(pin_rec[k % 2].data_ptr(), n, device=False)
+        return ctxs[k % NCTX].features_into(pin_rec[k % NCTX].data_ptr(), rec_cap, device=False)
 
-    e2e_steps = max(2, min(args.steps, 10))
-    for k in range(max(2, args.warmup)):
+    e2e_steps = max(NCTX, min(args.steps, 12))
+    for k in range(max(NCTX, args.warmup)):
         issue(k)
         finish(k)
     barrier()
-    s_a, s_b = stream, stream2
     e0 = torch.cuda.Event(enable_timing=True)
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s_a)
-    s_b.wait_event(e0)
+    e_end = [torch.cuda.Event(enable_timing=True) for _ in streams]
+    e0.record(streams[0])
+    for st in streams[1:]:
+        st.wait_event(e0)
     m = 0
     for k in range(e2e_steps):
         issue(k)
-        if k:
-            m = finish(k - 1)
-    m = finish(e2e_steps - 1)
-    ea.record(s_a)
-    eb.record(s_b)
-    ea.synchronize()
-    eb.synchronize()
+        if k >= NCTX - 1:
+            m = finish(k - (NCTX - 1))
+    for k in range(max(0, e2e_steps - (NCTX - 1)), e2e_steps):
+        m = finish(k)
+    for ev, st in zip(e_end, streams):
+        ev.record(st)
+    for ev in e_end:
+        ev.synchronize()
     barrier()
-    _, e2e_value = job_rate(max(e0.elapsed_time(ea), e0.elapsed_time(eb)), n, e2e_steps, world, dist, dev)
-    ctxs[1].close()
+    _, e2e_value = job_rate(max(e0.elapsed_time(ev) for ev in e_end), n, e2e_steps, world, dist, dev)
+    for cx in ctxs[1:]:
+        cx.close()
 
     # the link itself: one pinned H2D of the step's input, one D2H of its labels
     link = {}
@@ -550,7 +554,7 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "hits/s", "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 8 * n + CLUSTER_DTYPE.itemsize * m,
-                    "pipelining": "two contexts on two CUDA streams, steps alternating",
+                    "pipelining": "three contexts on three CUDA streams, steps in turn",
                     "link_gbs": link},
             "gpu_launches": n_kernels * args.steps,
             "clocks": clocks.summary(),
