@@ -86,3 +86,15 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower(), f
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without the compiled library the binding raises."""
+    from paper_2412_11809_gb300 import binding
+    saved = binding._lib
+    binding._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            binding.load_library(str(tmp_path / "libtpc.so"))
+    finally:
+        binding._lib = saved
