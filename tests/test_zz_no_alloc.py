@@ -33,12 +33,18 @@ def _reference(hits, w, h, dt):
         return c.labels(), c.features()
 
 
-def test_static_entry_matches_context_path_twice():
+@pytest.mark.parametrize("sensor", ["256x256", "448x512"])
+def test_static_entry_matches_context_path_twice(sensor):
     lib = binding.load_library()
-    hits, _ = synth.cfg1(scale=60000 / (64 * 2**20), seed=31)   # 60000 hits: 15 tiles, ragged tail
+    if sensor == "256x256":
+        w, h = 256, 256
+        hits, _ = synth.cfg1(scale=60000 / (64 * 2**20), seed=31)   # 60000 hits: 15 tiles, ragged tail
+    else:   # larger than the shared-memory pixel table: linked band by band
+        w, h = 448, 512
+        hits, _ = synth.cfg4(scale=60000 / (512 * 2**20), seed=32)
     n = len(hits)
     assert 4096 * 14 < n <= MAX_HITS
-    want_lab, want_rec = _reference(hits, 256, 256, 128)
+    want_lab, want_rec = _reference(hits, w, h, 128)
 
     d_hits = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).cuda()
     stream = torch.cuda.current_stream()
@@ -46,7 +52,7 @@ def test_static_entry_matches_context_path_twice():
         d_lab = torch.full((n,), -1, dtype=torch.int64, device="cuda")
         d_rec = torch.zeros((n, CLUSTER_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
         d_cnt = torch.full((2,), -1, dtype=torch.int64, device="cuda")
-        rc = lib.tpc_cluster_static(d_hits.data_ptr(), n, 256, 256, 128, d_lab.data_ptr(),
+        rc = lib.tpc_cluster_static(d_hits.data_ptr(), n, w, h, 128, d_lab.data_ptr(),
                                     d_rec.data_ptr(), n, d_cnt.data_ptr(),
                                     ctypes.c_void_p(stream.cuda_stream))
         assert rc == 0, binding.STATUS.get(rc, rc)
