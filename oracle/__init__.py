@@ -28,8 +28,11 @@ CLUSTER_DTYPE = np.dtype([("label", "<u8"), ("size", "<i8"), ("sum_tot", "<i8"),
                           ("first_toa", "<u8"), ("cx", "<f8"), ("cy", "<f8")])
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "tpc_oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+# TPC_ORACLE_SRC / TPC_ORACLE_BUILD point the oracle at another copy of its
+# source (tests/test_oracle_mutations.py plants mistakes in such copies to show
+# that the pins catch them); unset, the committed source is used.
+_SRC = os.environ.get("TPC_ORACLE_SRC") or os.path.join(_HERE, "tpc_oracle.c")
+_BUILD = os.environ.get("TPC_ORACLE_BUILD") or os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libtpc_oracle.so")
 _lock = threading.Lock()
 _lib = None
