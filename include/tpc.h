@@ -56,8 +56,9 @@ typedef struct tpc_cluster {
     int64_t sum_tot;    /* sum of ToT, exact */
     uint64_t first_toa; /* smallest ToA */
     float cx, cy;       /* ToT-weighted centroid sum(tot*x)/sum(tot), integer
-                           pixel coordinates, from exact integer sums rounded
-                           once to fp32; NaN when sum_tot == 0 */
+                           pixel coordinates: both exact integer sums taken to
+                           fp32 and divided in fp32 (relative error at most
+                           3 * 2^-24); NaN when sum_tot == 0 */
 } tpc_cluster;
 
 typedef enum {
@@ -92,7 +93,9 @@ typedef enum {
     /* cudaStream_t (cast to uint64_t) on which all work is ordered.
        Default 0 = a stream the context creates. */
     TPC_OPT_STREAM = 3,
-    /* CTAs per SM for the persistent kernels (0 = default / autotuned). */
+    /* At most this many CTAs per SM for the persistent kernels (each kernel's
+       grid is one wave: SMs x its occupancy).  0 (default) = as many as fit;
+       a smaller value leaves room for other work on the GPU. */
     TPC_OPT_CTAS_PER_SM = 4
 } tpc_option;
 
