@@ -181,6 +181,52 @@ int tpc_profile_flush(tpc_ctx *ctx, const char **names, float *ms, int cap, int 
 /* Bytes of device memory the context currently holds. */
 int tpc_device_bytes(tpc_ctx *ctx, size_t *bytes);
 
+/* Checkpoint of a streaming context (TPC_OPT_MAX_DISORDER set): everything
+   the next push depends on — the open hits carried on the device with their
+   global indices, the largest ToA seen, the watermark and the global index
+   of the next hit.  The paper's pipeline hands buffers over between
+   processing steps (Algorithm 2 and Algorithm 3, steps 1 and 9); a snapshot
+   taken between two pushes lets the stream continue in another context,
+   process or machine with results identical to an uninterrupted stream.
+   Byte layout (host order, little endian on every supported host):
+   tpc_snapshot_header, then n_carry tpc_hit records, then n_carry uint64
+   global indices, in the order the device keeps them. */
+#define TPC_SNAPSHOT_MAGIC 0x53435054u   /* "TPCS" */
+#define TPC_SNAPSHOT_VERSION 1u
+typedef struct tpc_snapshot_header {
+    uint32_t magic;         /* TPC_SNAPSHOT_MAGIC */
+    uint32_t version;       /* TPC_SNAPSHOT_VERSION */
+    uint32_t width, height; /* sensor of the context */
+    uint64_t dt;            /* time window of the context */
+    uint64_t max_disorder;  /* TPC_OPT_MAX_DISORDER of the context */
+    uint64_t pushed;        /* global index of the next hit to be pushed */
+    uint64_t seen_max;      /* largest ToA pushed so far (valid if has_seen) */
+    uint64_t watermark;     /* clusters whose last ToA <= watermark are final */
+    uint32_t has_seen;      /* 1 once any hit has been pushed */
+    uint32_t n_carry;       /* open hits carried into the next push */
+} tpc_snapshot_header;      /* 64 bytes */
+
+/* Write the snapshot of a streaming context into host memory `buf` (cap
+   bytes).  Waits for the context's queued work.  *n_out = bytes the
+   snapshot takes (64 + 24 * n_carry); if that exceeds cap (buf may then be
+   NULL), nothing is written and TPC_ERR_CAP is returned.  TPC_ERR_STATE for
+   a context not in streaming mode; a device-side error of the last push
+   (for example TPC_ERR_LATE) is returned instead of a snapshot.  The
+   context is left unchanged and may keep streaming. */
+int tpc_snapshot(tpc_ctx *ctx, void *buf, size_t cap, size_t *n_out);
+
+/* Load a snapshot (host memory, n bytes) into a TPC_LOCAL context created
+   with the same width, height and dt that holds no open hits and no
+   pending hits (new, or after tpc_flush).  Sets TPC_OPT_MAX_DISORDER to
+   the snapshot's and makes the context continue that stream: the next
+   push clusters its hits with the restored open hits, and global indices
+   continue from the header's `pushed`.  Results of earlier steps are
+   dropped (retrieval calls report nothing until the next push or flush).
+   TPC_ERR_ARG for a malformed snapshot (magic, version, size) or a sensor
+   or dt mismatch; TPC_ERR_STATE if the context is busy; the context is
+   unchanged on any error but TPC_ERR_CUDA and TPC_ERR_NOMEM. */
+int tpc_restore(tpc_ctx *ctx, const void *buf, size_t n);
+
 /* Largest batch tpc_cluster_static() accepts. */
 #define TPC_STATIC_MAX_HITS 65536
 

@@ -16,7 +16,12 @@ HIT_DTYPE = np.dtype([("x", "<u2"), ("y", "<u2"), ("tot", "<u2"),
                       ("reserved", "<u2"), ("toa", "<u8")])
 CLUSTER_DTYPE = np.dtype([("label", "<u8"), ("size", "<i8"), ("sum_tot", "<i8"),
                           ("first_toa", "<u8"), ("cx", "<f4"), ("cy", "<f4")])
+SNAPSHOT_HEADER_DTYPE = np.dtype([("magic", "<u4"), ("version", "<u4"), ("width", "<u4"),
+                                  ("height", "<u4"), ("dt", "<u8"), ("max_disorder", "<u8"),
+                                  ("pushed", "<u8"), ("seen_max", "<u8"), ("watermark", "<u8"),
+                                  ("has_seen", "<u4"), ("n_carry", "<u4")])
 assert HIT_DTYPE.itemsize == 16 and CLUSTER_DTYPE.itemsize == 40
+assert SNAPSHOT_HEADER_DTYPE.itemsize == 64
 
 TPC_HOST, TPC_DEVICE = 0, 1
 VARIANTS = {"local": 0, "global": 1, "static": 2, 0: 0, 1: 1, 2: 2}
@@ -44,6 +49,8 @@ SIGNATURES = {
     "tpc_device_bytes": ([_VP, ctypes.POINTER(_SZ)], _INT),
     "tpc_profile_flush": ([_VP, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                            _INT, ctypes.POINTER(_INT)], _INT),
+    "tpc_snapshot": ([_VP, _VP, _SZ, ctypes.POINTER(_SZ)], _INT),
+    "tpc_restore": ([_VP, _VP, _SZ], _INT),
     "tpc_cluster_static": ([_VP, _SZ, _U32, _U32, _U64, _VP, _VP, _SZ, _VP, _VP], _INT),
     "tpc_strerror": ([_INT], ctypes.c_char_p),
     "tpc_destroy": ([_VP], None),
@@ -227,6 +234,22 @@ class Clusterer:
         _check(self._lib.tpc_profile_flush(self._h, names, ms, cap, ctypes.byref(n)),
                "tpc_profile_flush")
         return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
+
+    def snapshot(self) -> bytes:
+        """Checkpoint of a streaming context's open state (``tpc_snapshot``)."""
+        n = ctypes.c_size_t()
+        rc = self._lib.tpc_snapshot(self._h, None, 0, ctypes.byref(n))
+        if rc != -7:   # TPC_ERR_CAP: the size query
+            _check(rc, "tpc_snapshot")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._lib.tpc_snapshot(self._h, buf, n.value, ctypes.byref(n)), "tpc_snapshot")
+        return buf.raw[:n.value]
+
+    def restore(self, snap: bytes):
+        """Continue the stream a snapshot was taken of (``tpc_restore``)."""
+        buf = ctypes.create_string_buffer(bytes(snap), len(snap))
+        _check(self._lib.tpc_restore(self._h, buf, len(snap)), "tpc_restore")
+        self._keep.clear()
 
     def device_bytes(self) -> int:
         b = ctypes.c_size_t()

@@ -3,9 +3,13 @@
 //
 // A processing step (tpc_flush, a streaming tpc_push, or tpc_batch_flush)
 // enqueues the same fixed kernel sequence on one CUDA stream:
-//   setup -> prepare (load, validate, ToA min/max) -> finalize -> keys ->
-//   radix passes 0..3 -> gather -> tile link -> border link -> flatten ->
-//   accumulate -> labels -> tile scan -> records -> stream compact -> end.
+//   setup -> tile sort -> tile merge -> sort check -> segment finalize ->
+//   (general-order fallback: keys -> radix passes 0..3 -> gather) ->
+//   table link -> tile link (redo tiles) -> border fast -> border link ->
+//   flatten -> accumulate -> labels -> tile scan -> records ->
+//   stream compact -> stream end.
+// Streaming contexts also checkpoint and restore their open state here
+// (tpc_snapshot / tpc_restore).
 // Every size the kernels need is read from device memory and every kernel is
 // a persistent grid over (segment, tile) work items, so no step waits for the
 // host and the sequence is captured once into a CUDA graph and replayed.
@@ -879,6 +883,111 @@ int tpc_device_bytes(tpc_ctx *c, size_t *bytes) {
     if (!c || !bytes) return TPC_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     *bytes = c->device_bytes();
+    return TPC_OK;
+}
+
+static_assert(sizeof(tpc_snapshot_header) == 64, "snapshot header layout");
+
+int tpc_snapshot(tpc_ctx *c, void *buf, size_t cap, size_t *n_out) {
+    if (!c || !n_out) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->max_disorder == ~0ull || !c->ss) return TPC_ERR_STATE;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (c->has_result) {
+        Prob p;
+        if (cudaMemcpy(&p, c->res_prob, sizeof(Prob), cudaMemcpyDeviceToHost) != cudaSuccess) return TPC_ERR_CUDA;
+        if (p.err) return map_err(p.err);
+    }
+    StreamState st;
+    if (cudaMemcpy(&st, c->ss, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return TPC_ERR_CUDA;
+    const size_t nc = c->sbuf[0] ? st.n_carry : 0;
+    const size_t bytes = sizeof(tpc_snapshot_header) + nc * (sizeof(tpc_hit) + sizeof(uint64_t));
+    *n_out = bytes;
+    if (bytes > cap) return TPC_ERR_CAP;
+    if (!buf) return TPC_ERR_ARG;
+    tpc_snapshot_header h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = TPC_SNAPSHOT_MAGIC;
+    h.version = TPC_SNAPSHOT_VERSION;
+    h.width = c->width;
+    h.height = c->height;
+    h.dt = c->dt;
+    h.max_disorder = c->max_disorder;
+    h.pushed = c->pushed;
+    h.seen_max = st.seen_max;
+    h.watermark = st.watermark;
+    h.has_seen = st.has_seen ? 1u : 0u;
+    h.n_carry = (uint32_t)nc;
+    char *out = static_cast<char *>(buf);
+    std::memcpy(out, &h, sizeof(h));
+    if (nc) {
+        // the carry sits right-aligned in the buffer the next step reads
+        const int next = 1 - c->scur;
+        if (cudaMemcpy(out + sizeof(h), c->sbuf[next] + (c->carry_cap - nc), nc * sizeof(tpc_hit),
+                       cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(out + sizeof(h) + nc * sizeof(tpc_hit), c->sgidx[next] + (c->carry_cap - nc),
+                       nc * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return TPC_ERR_CUDA;
+    }
+    return TPC_OK;
+}
+
+int tpc_restore(tpc_ctx *c, const void *buf, size_t n) {
+    if (!c || !buf || n < sizeof(tpc_snapshot_header)) return TPC_ERR_ARG;
+    tpc_snapshot_header h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != TPC_SNAPSHOT_MAGIC || h.version != TPC_SNAPSHOT_VERSION) return TPC_ERR_ARG;
+    if (n != sizeof(h) + (size_t)h.n_carry * (sizeof(tpc_hit) + sizeof(uint64_t))) return TPC_ERR_ARG;
+    if (h.max_disorder == 0 || h.max_disorder == ~0ull || h.has_seen > 1) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (h.width != c->width || h.height != c->height || h.dt != c->dt || c->variant != TPC_LOCAL)
+        return TPC_ERR_ARG;
+    if (c->pending || c->zc) return TPC_ERR_STATE;
+    if (c->ss && c->carry_ub) {
+        // carry_ub only bounds the carry: read the exact count
+        uint32_t open = 0;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+            cudaMemcpy(&open, &c->ss->n_carry, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return TPC_ERR_CUDA;
+        if (open) return TPC_ERR_STATE;
+        c->carry_ub = 0;
+    }
+    if (!c->ss) {
+        if (cudaMalloc(&c->ss, sizeof(StreamState)) != cudaSuccess) return TPC_ERR_NOMEM;
+        if (cudaMemsetAsync(c->ss, 0, sizeof(StreamState), c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+        c->scur = 1;
+        c->carry_ub = 0;
+    }
+    // Room for the restored carry, grown while the device still holds an empty
+    // carry (nothing is moved); then the open hits and the stream state.
+    const size_t nc = h.n_carry;
+    int rc = ensure_stream_buffers(c, nc);
+    if (rc) return rc;
+    StreamState st;
+    std::memset(&st, 0, sizeof(st));
+    st.n_carry = h.n_carry;
+    st.has_seen = h.has_seen;
+    st.seen_max = h.seen_max;
+    st.watermark = h.watermark;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+        cudaMemcpy(c->ss, &st, sizeof(st), cudaMemcpyHostToDevice) != cudaSuccess)
+        return TPC_ERR_CUDA;
+    if (nc) {
+        const char *src = static_cast<const char *>(buf) + sizeof(h);
+        const int next = 1 - c->scur;
+        if (cudaMemcpy(c->sbuf[next] + (c->carry_cap - nc), src, nc * sizeof(tpc_hit), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(c->sgidx[next] + (c->carry_cap - nc), src + nc * sizeof(tpc_hit), nc * sizeof(uint64_t),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return TPC_ERR_CUDA;
+    }
+    c->max_disorder = h.max_disorder;
+    c->carry_ub = nc;
+    c->pushed = h.pushed;
+    c->base = h.pushed;
+    c->has_result = false;
+    c->res_streaming = false;
+    c->res_base = h.pushed;
     return TPC_OK;
 }
 

@@ -50,6 +50,16 @@ def test_strerror_without_gpu(lib):
     assert lib.tpc_strerror(12345) == b"unknown status"
 
 
+def test_checkpoint_argument_checks_without_gpu(lib):
+    """Argument checks come before any CUDA call (no context needed)."""
+    import ctypes
+    n = ctypes.c_size_t()
+    assert lib.tpc_snapshot(None, None, 0, ctypes.byref(n)) == -1
+    assert lib.tpc_restore(None, None, 0) == -1
+    buf = ctypes.create_string_buffer(64)
+    assert lib.tpc_restore(None, buf, 64) == -1
+
+
 def test_record_layout_in_c():
     src = r'''
 #include <stddef.h>
@@ -59,6 +69,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tpc_hit), offsetof(tpc_hit, toa),
          offsetof(tpc_hit, tot), sizeof(tpc_cluster), offsetof(tpc_cluster, first_toa),
          offsetof(tpc_cluster, cx));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(tpc_snapshot_header), offsetof(tpc_snapshot_header, dt),
+         offsetof(tpc_snapshot_header, pushed), offsetof(tpc_snapshot_header, watermark),
+         offsetof(tpc_snapshot_header, n_carry));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -70,9 +83,12 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
                                                check=True).stdout.split()]
     from paper_2412_11809_gb300 import CLUSTER_DTYPE, HIT_DTYPE
+    from paper_2412_11809_gb300.binding import SNAPSHOT_HEADER_DTYPE as S
     assert vals == [HIT_DTYPE.itemsize, HIT_DTYPE.fields["toa"][1], HIT_DTYPE.fields["tot"][1],
                     CLUSTER_DTYPE.itemsize, CLUSTER_DTYPE.fields["first_toa"][1],
-                    CLUSTER_DTYPE.fields["cx"][1]]
+                    CLUSTER_DTYPE.fields["cx"][1],
+                    S.itemsize, S.fields["dt"][1], S.fields["pushed"][1],
+                    S.fields["watermark"][1], S.fields["n_carry"][1]]
 
 
 def test_product_path_does_not_import_oracle():
