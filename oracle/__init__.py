@@ -12,6 +12,8 @@ gcc); this module only marshals numpy arrays:
   of the paper's cluster definition (Section 2, conditions (i)-(iii)).
 * ``features(hits, labels)`` — per-cluster size, sum ToT, first ToA and the
   ToT-weighted centroid (fp64), ordered by label.
+* ``fill_buffers(hits, b, b_t, t, t_closing)`` — the host-side hit buffer
+  filling of Algorithm 2: which buffer each hit is sent in.
 """
 from __future__ import annotations
 
@@ -66,6 +68,11 @@ def _load():
         lib.oracle_features.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
         lib.oracle_features.restype = ctypes.c_int
+        lib.oracle_fill_buffers.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_uint64)]
+        lib.oracle_fill_buffers.restype = ctypes.c_int
         lib.oracle_hit_size.restype = ctypes.c_uint32
         lib.oracle_cluster_size.restype = ctypes.c_uint32
         assert lib.oracle_hit_size() == HIT_DTYPE.itemsize
@@ -112,6 +119,26 @@ def features(hits, lab) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"oracle: {_ERRORS.get(rc, rc)}")
     return out[: m.value].copy()
+
+
+def fill_buffers(hits, b: int, b_t: int, t: int, t_closing: int):
+    """Algorithm 2 (hit buffer filling) over the hits in arrival order.
+
+    Returns ``(buffer_of, cut)``: the number of the buffer each hit lands in
+    (buffers numbered in the order they are sent) and, per buffer, the closing
+    time ``toa_max + t_closing`` at which it was sent (``2**64 - 1`` for the
+    buffers sent at the end of the stream)."""
+    h = _as_hits(hits)
+    n = len(h)
+    buffer_of = np.empty(n, dtype=np.uint64)
+    cut = np.empty(n + 1, dtype=np.uint64)
+    m = ctypes.c_uint64(0)
+    rc = _load().oracle_fill_buffers(h.ctypes.data if n else None, n, b, b_t, t, t_closing,
+                                     buffer_of.ctypes.data if n else None, cut.ctypes.data,
+                                     ctypes.byref(m))
+    if rc != 0:
+        raise ValueError(f"oracle: {_ERRORS.get(rc, rc)}")
+    return buffer_of, cut[: m.value].copy()
 
 
 def make_hits(x, y, toa, tot=None) -> np.ndarray:

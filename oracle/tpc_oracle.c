@@ -336,5 +336,64 @@ int oracle_features(const or_hit *h, uint64_t n, const uint64_t *label,
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Hit buffer filling (Algorithm 2, Section 4.1): the host-side procedure     */
+/* storeHit(hit, buffer, nextBuffer), called once per hit in arrival order.  */
+/*   b         maximum buffer size                                           */
+/*   b_t       room kept free at the end of a buffer for late hits            */
+/*   t         the stream's disorder bound (the stream is t-ordered)          */
+/*   t_closing slack added to toa_max to place the buffer's closing time      */
+/* A buffer takes hits freely while it holds fewer than b - b_t; after that   */
+/* only hits earlier than toa_max + t_closing, the rest go to the next        */
+/* buffer; a hit later than toa_max + t + t_closing sends the buffer, and the */
+/* next buffer becomes the current one.  toa_max is one variable for the      */
+/* whole stream, updated only by hits taken while the buffer has room, as the */
+/* procedure states.                                                          */
+/* Readings where the procedure is silent: b caps the closing phase, so a    */
+/* hit that qualifies for a full buffer (b hits) goes to the next buffer (the */
+/* next buffer itself has no cap in the procedure); at the end of the stream */
+/* the current buffer and then a non-empty next buffer are sent.             */
+/* Output: buffer_of[i] = number of the buffer hit i lands in (buffers are    */
+/* numbered in the order they are sent; inside a buffer hits keep arrival    */
+/* order); cut[k] = toa_max + t_closing when buffer k was sent (saturating;  */
+/* UINT64_MAX for buffers sent at the end); *n_buffers = buffers sent.        */
+/* cut must hold n + 1 entries.                                               */
+
+static uint64_t sat_add(uint64_t a, uint64_t b) { return a > UINT64_MAX - b ? UINT64_MAX : a + b; }
+
+int oracle_fill_buffers(const or_hit *h, uint64_t n, uint64_t b, uint64_t b_t, uint64_t t,
+                        uint64_t t_closing, uint64_t *buffer_of, uint64_t *cut,
+                        uint64_t *n_buffers) {
+    if ((n && (!h || !buffer_of)) || !cut || !n_buffers || b == 0 || b_t >= b) return OR_ERR_ARG;
+    uint64_t toa_max = 0;
+    uint64_t cur = 0;          /* number of the current buffer; the next one is cur + 1 */
+    uint64_t size_cur = 0, size_next = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t toa = h[i].toa;
+        if (size_cur < b - b_t) {
+            buffer_of[i] = cur;
+            size_cur++;
+            if (toa > toa_max) toa_max = toa;
+        } else if (toa < sat_add(toa_max, t_closing) && size_cur < b) {
+            buffer_of[i] = cur;
+            size_cur++;
+        } else {
+            buffer_of[i] = cur + 1;
+            size_next++;
+        }
+        if (toa > toa_max && toa - toa_max > sat_add(t, t_closing)) {
+            cut[cur] = sat_add(toa_max, t_closing);   /* sendToDevice(buffer) */
+            cur++;                                     /* buffer <- nextBuffer */
+            size_cur = size_next;
+            size_next = 0;
+        }
+    }
+    uint64_t sent = cur;
+    if (size_cur) cut[sent++] = UINT64_MAX;
+    if (size_next) cut[sent++] = UINT64_MAX;
+    *n_buffers = sent;
+    return OR_OK;
+}
+
 uint32_t oracle_hit_size(void) { return (uint32_t)sizeof(or_hit); }
 uint32_t oracle_cluster_size(void) { return (uint32_t)sizeof(or_cluster); }

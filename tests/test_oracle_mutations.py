@@ -1,6 +1,7 @@
 """The oracle's pins catch plausible mistakes: each mistake below is planted
 in a copy of the oracle's C source (never the committed file), the copy is
-compiled, and the oracle pin suite (tests/test_oracle.py) must fail on it."""
+compiled, and the oracle pin suites (tests/test_oracle.py and
+tests/test_oracle_filling.py) must fail on it."""
 import os
 import subprocess
 import sys
@@ -28,7 +29,14 @@ MISTAKES = {
         "uint64_t f = u.first[r] < u.first[root] ? u.first[r] : u.first[root];",
         "uint64_t f = u.first[r];"),
     "centroid weights missing": ("swx[c] += (uint64_t)h[i].tot * h[i].x;", "swx[c] += (uint64_t)h[i].x;"),
+    "closing time inclusive": ("} else if (toa < sat_add(toa_max, t_closing) && size_cur < b) {",
+                               "} else if (toa <= sat_add(toa_max, t_closing) && size_cur < b) {"),
+    "toa_max not kept while filling": ("if (toa > toa_max) toa_max = toa;", ";"),
+    "send trigger without the disorder bound": ("toa - toa_max > sat_add(t, t_closing)",
+                                                "toa - toa_max > t_closing"),
+    "closing phase without room check": ("if (size_cur < b - b_t) {", "if (size_cur < b) {"),
 }
+PIN_FILES = ["test_oracle.py", "test_oracle_filling.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MISTAKES))
@@ -39,7 +47,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     mutant = tmp_path / "tpc_oracle.c"
     mutant.write_text(src.replace(good, bad))
     env = dict(os.environ, TPC_ORACLE_SRC=str(mutant), TPC_ORACLE_BUILD=str(tmp_path / "build"))
-    out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle.py"),
+    out = subprocess.run([sys.executable, "-m", "pytest",
+                          *[os.path.join(ROOT, "tests", f) for f in PIN_FILES],
                           "-x", "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env,
                          capture_output=True, text=True, timeout=600)
     assert out.returncode != 0, f"planted mistake '{name}' passed every pin:\n{out.stdout[-2000:]}"
