@@ -71,14 +71,25 @@ def path_bytes_per_hit(n_hits: int, n_clusters: int) -> float:
     return 16 + 8 + 40 * n_clusters / max(n_hits, 1)
 
 
+# Device-code sources: every kernel of a processing step with its launch
+# configuration.  The launch order lives in the API file's enqueue_kernels(),
+# hashed on its own; the rest of that file (context bookkeeping, checkpoints)
+# and the host-side buffer filling are not part of any kernel.
+KERNEL_SOURCES = ("features.cu", "link.cu", "noalloc.cu", "prepare.cu", "radix.cu", "sortfast.cu",
+                  "tpc_internal.cuh", "variants.cu")
+
+
 def kernel_source_sha() -> str:
-    """Hash of the CUDA sources: a stored ncu traffic figure is only valid for the
-    build it was captured on."""
-    import glob
+    """Hash of the device-code sources and the launch sequence: a stored ncu
+    traffic figure is only valid for the kernels it was captured on."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2412_11809_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2412_11809_gb300", "csrc", "*.cu*"))):
-        h.update(open(f, "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    api = open(os.path.join(csrc, "tpc_api.cu")).read()
+    start = api.index("void enqueue_kernels(")
+    h.update(api[start:api.index("\n}\n", start)].encode())
     return h.hexdigest()[:16]
 
 
@@ -352,6 +363,57 @@ def run_large_sensor(args, dev, torch):
     return out
 
 
+def run_ingest(hits, t, dev, torch, chunk=2**20):
+    """Host-side ingestion (Algorithm 2, then Algorithm 3 steps 1-2): the
+    stream arrives in chunks of `chunk` hits.  (1) The hit buffer filling on
+    one host thread, each sent buffer taken (copied out with its arrival
+    numbers) at once; the stream runs twice through one filler, the second
+    time shifted later by its span, and the second pass is timed (buffers
+    recycled, as in a long-running stream).  (2) Filling plus sendToDevice
+    into a streaming context (max_disorder = the stream's t) with every
+    step's labels and their indices read back to host memory, timed on the
+    host clock from the first stored chunk to the last label (a fresh
+    context: its first-use allocations are inside)."""
+    from paper_2412_11809_gb300 import Clusterer, Filler
+    from paper_2412_11809_gb300.binding import HIT_DTYPE
+    n = len(hits)
+    b, b_t, t_closing = 8 * 2**20, 2**20, 2 * DT
+    out_h = np.zeros(2 * b, dtype=HIT_DTYPE)
+    out_i = np.zeros(2 * b, dtype=np.uint64)
+    later = hits.copy()
+    later["toa"] += np.uint64(int(hits["toa"].max()) - int(hits["toa"].min()) + 2 * t)
+    nbuf = 0
+    with Filler(b, b_t, t, t_closing) as f:
+        for stream_pass, src in enumerate((hits, later)):
+            t0 = time.perf_counter()
+            for s in range(0, n, chunk):
+                f.store(src[s:s + chunk])
+                while f.take_into(out_h, out_i) is not None:
+                    nbuf += stream_pass
+            t_fill = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=dev)
+    got = 0
+    with Clusterer(W, H, DT, max_disorder=t, stream=stream) as c, Filler(b, b_t, t, t_closing) as f:
+        t0 = time.perf_counter()
+        for s in range(0, n + chunk, chunk):
+            if s < n:
+                f.store(hits[s:s + chunk])
+            else:
+                f.finish()
+            while f.send(c) is not None:
+                lab, _ = c.labels(with_indices=True)
+                got += len(lab)
+        c.flush()
+        lab, _ = c.labels(with_indices=True)
+        got += len(lab)
+        t_pipe = time.perf_counter() - t0
+    if got != n:
+        raise RuntimeError(f"ingest pipeline finalised {got} of {n} hits")
+    return {"filler_hits_s": n / t_fill, "pipeline_hits_s": n / t_pipe, "buffers_per_pass": nbuf,
+            "b": b, "b_t": b_t, "t": t, "t_closing": t_closing, "store_chunk": chunk,
+            "hits": n, "threads": 1}
+
+
 def run_batched(args, dev, torch):
     """16 detectors (ten 256x256, six 448x512): one batched step (one CUDA-graph
     replay, persistent CTAs over every detector's tiles) against one flush per
@@ -408,7 +470,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    hits, _ = synth.cfg1(scale=args.scale, seed=1000 + rank)
+    hits, t_disorder = synth.cfg1(scale=args.scale, seed=1000 + rank)
     n = len(hits)
     host_u8 = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16))
     d_hits = host_u8.to(dev)
@@ -528,11 +590,17 @@ def run_gpu(args):
                "sample": f"first {n_sample} hits of the same stream, labels + features, "
                          f"single-threaded on a host with {cpu_cores()} cores"}
 
-    serving = batched = large = None
+    serving = batched = large = ingest = None
     if rank == 0 and not args.no_extras:
-        batched = run_batched(args, dev, torch)
-        serving = run_serving(args, dev, torch)
-        large = run_large_sensor(args, dev, torch)
+        def extra(fn, *a):
+            try:
+                return fn(*a)
+            except Exception as e:   # reported in the JSON line, never fatal
+                return {"error": f"{type(e).__name__}: {e}"}
+        batched = extra(run_batched, args, dev, torch)
+        serving = extra(run_serving, args, dev, torch)
+        large = extra(run_large_sensor, args, dev, torch)
+        ingest = extra(run_ingest, hits, t_disorder, dev, torch)
 
     if rank == 0:
         line = {
@@ -561,6 +629,7 @@ def run_gpu(args):
             "serving": serving,
             "batched": batched,
             "large_sensor": large,
+            "ingest": ingest,
         }
         print(json.dumps(line), flush=True)
     c.close()
@@ -579,7 +648,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16 * 2**20)
     ap.add_argument("--ref-sample", type=int, default=4 * 2**20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the serving and batched lines")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, serving, large-sensor and ingest lines")
     ap.add_argument("--serving-hits", type=int, default=4 * 2**20, help="base hits per serving stream")
     ap.add_argument("--serving-chunks", type=int, default=1024)
     ap.add_argument("--batch-scale", type=float, default=1.0)

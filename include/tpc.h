@@ -227,6 +227,57 @@ int tpc_snapshot(tpc_ctx *ctx, void *buf, size_t cap, size_t *n_out);
    unchanged on any error but TPC_ERR_CUDA and TPC_ERR_NOMEM. */
 int tpc_restore(tpc_ctx *ctx, const void *buf, size_t n);
 
+/* Hit buffer filling (Algorithm 2, Section 4.1): host-side ingestion that
+   cuts a t-ordered hit stream (Section 3.1: toa_i < toa_j + t for every
+   earlier hit i and later hit j) into buffers for the device.  A buffer
+   takes hits freely while it holds fewer than b - b_t; then only hits
+   earlier than toa_max + t_closing (and while it holds fewer than b); other
+   hits go to the next buffer.  A hit later than toa_max + t + t_closing
+   sends the buffer, and the next buffer becomes the current one.  toa_max
+   is the largest ToA of the hits taken while a buffer had room, one value
+   for the whole stream.  On a t-ordered stream whose closing windows fit in
+   b_t, buffer k holds exactly the hits earlier than its cut toa_max +
+   t_closing, so clusters are split only across a cut, within dt of it; in
+   every case the buffers, taken in the order they are sent, form a
+   t-ordered stream again.  Buffers keep arrival order inside; the next
+   buffer has no size cap, so a buffer can start with more than b hits when
+   b_t is too small for the stream.  Host memory only (no CUDA call); a
+   filler must not be used from two host threads at once. */
+typedef struct tpc_filler tpc_filler;
+
+/* b > b_t >= 0 (TPC_ERR_ARG otherwise); t, t_closing in ToA ticks. */
+int tpc_filler_create(uint64_t b, uint64_t b_t, uint64_t t, uint64_t t_closing,
+                      tpc_filler **out);
+
+/* storeHit for each of the n host hits, in order.  Hits are numbered in
+   arrival order over all calls (0-based).  TPC_ERR_STATE after
+   tpc_filler_finish(). */
+int tpc_filler_store(tpc_filler *f, const tpc_hit *hits, size_t n);
+
+/* End of the stream: send the current buffer, then a non-empty next
+   buffer (their cut is UINT64_MAX). */
+int tpc_filler_finish(tpc_filler *f);
+
+/* Number of sent buffers waiting, and the size in hits of the oldest (0 if
+   none); either pointer may be NULL. */
+int tpc_filler_ready(tpc_filler *f, size_t *n_buffers, size_t *front_hits);
+
+/* Take the oldest sent buffer: its hits into `hits` (host, cap records),
+   their arrival numbers into `indices` (host, cap entries, may be NULL) and
+   its cut into *cut (may be NULL).  *n_out = its size; TPC_ERR_CAP (nothing
+   taken) if that exceeds cap; TPC_ERR_STATE if no buffer is waiting. */
+int tpc_filler_take(tpc_filler *f, tpc_hit *hits, uint64_t *indices, size_t cap,
+                    size_t *n_out, uint64_t *cut);
+
+/* sendToDevice: push the oldest sent buffer into a context (tpc_push of
+   host hits, so the same ordering and errors) and take it; arrival numbers,
+   size and cut as tpc_filler_take.  On an error of tpc_push the buffer
+   stays waiting. */
+int tpc_filler_send(tpc_filler *f, tpc_ctx *ctx, uint64_t *indices, size_t cap,
+                    size_t *n_out, uint64_t *cut);
+
+void tpc_filler_destroy(tpc_filler *f);
+
 /* Largest batch tpc_cluster_static() accepts. */
 #define TPC_STATIC_MAX_HITS 65536
 

@@ -52,6 +52,13 @@ SIGNATURES = {
     "tpc_snapshot": ([_VP, _VP, _SZ, ctypes.POINTER(_SZ)], _INT),
     "tpc_restore": ([_VP, _VP, _SZ], _INT),
     "tpc_cluster_static": ([_VP, _SZ, _U32, _U32, _U64, _VP, _VP, _SZ, _VP, _VP], _INT),
+    "tpc_filler_create": ([_U64, _U64, _U64, _U64, ctypes.POINTER(_VP)], _INT),
+    "tpc_filler_store": ([_VP, _VP, _SZ], _INT),
+    "tpc_filler_finish": ([_VP], _INT),
+    "tpc_filler_ready": ([_VP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)], _INT),
+    "tpc_filler_take": ([_VP, _VP, _VP, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_U64)], _INT),
+    "tpc_filler_send": ([_VP, _VP, _VP, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_U64)], _INT),
+    "tpc_filler_destroy": ([_VP], None),
     "tpc_strerror": ([_INT], ctypes.c_char_p),
     "tpc_destroy": ([_VP], None),
 }
@@ -280,3 +287,89 @@ def batch_flush(clusterers) -> None:
     lib = load_library()
     arr = (ctypes.c_void_p * len(clusterers))(*[c.handle.value for c in clusterers])
     _check(lib.tpc_batch_flush(arr, len(clusterers)), "tpc_batch_flush")
+
+
+class Filler:
+    """Hit buffer filling (Algorithm 2), see ``tpc_filler_create``.  Host-side:
+    ``store`` hits in arrival order, then ``take`` or ``send`` the buffers it
+    has sent, oldest first."""
+
+    def __init__(self, b: int, b_t: int, t: int, t_closing: int):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.tpc_filler_create(b, b_t, t, t_closing, ctypes.byref(h)), "tpc_filler_create")
+        self._h, self._lib = h, lib
+
+    def store(self, hits):
+        a = np.ascontiguousarray(hits)
+        if a.dtype != HIT_DTYPE:
+            raise TypeError(f"hits must have dtype {HIT_DTYPE}")
+        _check(self._lib.tpc_filler_store(self._h, a.ctypes.data if len(a) else None, len(a)),
+               "tpc_filler_store")
+
+    def finish(self):
+        _check(self._lib.tpc_filler_finish(self._h), "tpc_filler_finish")
+
+    def ready(self) -> tuple[int, int]:
+        """(buffers waiting, hits in the oldest)."""
+        nb, nh = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self._lib.tpc_filler_ready(self._h, ctypes.byref(nb), ctypes.byref(nh)),
+               "tpc_filler_ready")
+        return nb.value, nh.value
+
+    def take(self):
+        """The oldest sent buffer as (hits, arrival indices, cut), or None."""
+        nb, nh = self.ready()
+        if not nb:
+            return None
+        hits = np.empty(nh, dtype=HIT_DTYPE)
+        idx = np.empty(nh, dtype=np.uint64)
+        n, cut = ctypes.c_size_t(), ctypes.c_uint64()
+        _check(self._lib.tpc_filler_take(self._h, hits.ctypes.data, idx.ctypes.data, nh,
+                                         ctypes.byref(n), ctypes.byref(cut)), "tpc_filler_take")
+        return hits, idx, cut.value
+
+    def take_into(self, hits, indices=None):
+        """Take the oldest sent buffer into caller arrays (HIT_DTYPE records,
+        uint64 indices or None); returns (n, cut), or None if none is waiting."""
+        if hits.dtype != HIT_DTYPE or not hits.flags.c_contiguous:
+            raise TypeError("hits must be a contiguous HIT_DTYPE array")
+        if indices is not None and (indices.dtype != np.uint64 or len(indices) < len(hits)
+                                    or not indices.flags.c_contiguous):
+            raise TypeError("indices must be a contiguous uint64 array at least as long as hits")
+        n, cut = ctypes.c_size_t(), ctypes.c_uint64()
+        rc = self._lib.tpc_filler_take(self._h, hits.ctypes.data, None if indices is None else
+                                       indices.ctypes.data, len(hits), ctypes.byref(n), ctypes.byref(cut))
+        if rc == -10:    # TPC_ERR_STATE: no buffer waiting
+            return None
+        _check(rc, "tpc_filler_take")
+        return n.value, cut.value
+
+    def send(self, clusterer):
+        """sendToDevice: push the oldest sent buffer into a Clusterer; returns
+        (arrival indices, cut), or None if no buffer is waiting."""
+        nb, nh = self.ready()
+        if not nb:
+            return None
+        idx = np.empty(nh, dtype=np.uint64)
+        n, cut = ctypes.c_size_t(), ctypes.c_uint64()
+        _check(self._lib.tpc_filler_send(self._h, clusterer.handle, idx.ctypes.data, nh,
+                                         ctypes.byref(n), ctypes.byref(cut)), "tpc_filler_send")
+        return idx, cut.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tpc_filler_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
