@@ -93,7 +93,7 @@ int main(void) {
 
 def test_product_path_does_not_import_oracle():
     """The CUDA path and the oracle share no code: nothing under the package
-    imports, links or reads oracle/."""
+    imports, links or reads oracle/ (nor the CPU comparison baseline)."""
     pkg = os.path.join(ROOT, "paper_2412_11809_gb300")
     for dirpath, _, files in os.walk(pkg):
         if "_build" in dirpath:
@@ -102,6 +102,7 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower(), f
+                assert "cpu_baseline" not in text and "tsplit" not in text, f
 
 
 def test_missing_library_fails_loudly(tmp_path):
