@@ -611,7 +611,10 @@ def run_gpu(args):
 
     cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_par = cpu_parallel_sample(hits)
+        try:
+            cpu_par = cpu_parallel_sample(hits)
+        except Exception as e:   # reported in the JSON line, never fatal
+            cpu_par = {"error": f"{type(e).__name__}: {e}"}
 
     serving = batched = large = ingest = None
     if rank == 0 and not args.no_extras:
