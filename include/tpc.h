@@ -96,7 +96,15 @@ typedef enum {
     /* At most this many CTAs per SM for the persistent kernels (each kernel's
        grid is one wave: SMs x its occupancy).  0 (default) = as many as fit;
        a smaller value leaves room for other work on the GPU. */
-    TPC_OPT_CTAS_PER_SM = 4
+    TPC_OPT_CTAS_PER_SM = 4,
+    /* Fault injection on the host, for tests of error handling: value N > 0
+       makes the N-th device or pinned allocation this context makes from
+       now on fail as an out-of-memory would (the call reports
+       TPC_ERR_NOMEM); it fires once, then the option is off.  0 = off.  No
+       CUDA call fails and no GPU is faulted: the allocation is not made.
+       After any TPC_ERR_NOMEM the context stays usable and the failed call
+       may be repeated; the result of the step before is dropped. */
+    TPC_OPT_FAIL_ALLOC = 5
 } tpc_option;
 
 typedef struct tpc_ctx tpc_ctx;

@@ -25,7 +25,7 @@ assert SNAPSHOT_HEADER_DTYPE.itemsize == 64
 
 TPC_HOST, TPC_DEVICE = 0, 1
 VARIANTS = {"local": 0, "global": 1, "static": 2, 0: 0, 1: 1, 2: 2}
-OPT_MAX_DISORDER, OPT_MEM_BUDGET, OPT_STREAM, OPT_CTAS_PER_SM = 1, 2, 3, 4
+OPT_MAX_DISORDER, OPT_MEM_BUDGET, OPT_STREAM, OPT_CTAS_PER_SM, OPT_FAIL_ALLOC = 1, 2, 3, 4, 5
 
 STATUS = {0: "TPC_OK", -1: "TPC_ERR_ARG", -2: "TPC_ERR_RANGE", -3: "TPC_ERR_NOMEM",
           -4: "TPC_ERR_BUSY", -5: "TPC_ERR_TIMEOUT", -6: "TPC_ERR_CUDA", -7: "TPC_ERR_CAP",
@@ -136,6 +136,15 @@ class Clusterer:
     @property
     def handle(self):
         return self._h
+
+    def set_option(self, key: int, value: int):
+        """``tpc_set_option`` (see ``tpc_option``; e.g. ``OPT_MAX_DISORDER``)."""
+        _check(self._lib.tpc_set_option(self._h, key, value), "tpc_set_option")
+
+    def inject_alloc_failure(self, nth: int):
+        """Test hook: the nth allocation from now fails as an out-of-memory
+        would (``TPC_OPT_FAIL_ALLOC``); 0 turns it off."""
+        self.set_option(OPT_FAIL_ALLOC, nth)
 
     def push(self, hits):
         """Append a chunk: a numpy array of HIT_DTYPE (host) or a CUDA tensor."""

@@ -42,16 +42,35 @@ std::mutex occ_mu;
 std::vector<OccEntry> occ_cache;
 
 
+// Every allocation of a context goes through these two.  `fault` is the
+// context's TPC_OPT_FAIL_ALLOC countdown (a test hook): while positive it
+// counts the allocations still to succeed, and the one that brings it to
+// zero fails as an out-of-memory would, without calling CUDA.
+bool injected_failure(int64_t *fault) { return fault && *fault > 0 && --*fault == 0; }
+
+cudaError_t dev_alloc(int64_t *fault, void **p, size_t bytes) {
+    *p = nullptr;
+    if (injected_failure(fault)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc(int64_t *fault, void **p, size_t bytes) {
+    *p = nullptr;
+    if (injected_failure(fault)) return cudaErrorMemoryAllocation;
+    return cudaMallocHost(p, bytes);
+}
+
 struct DevMem {
     std::vector<void *> ptrs;
     size_t bytes = 0;
+    int64_t *fault = nullptr;
     template <class T>
     T *alloc(size_t count, cudaError_t &err) {
         void *p = nullptr;
         if (err != cudaSuccess) return nullptr;
         size_t b = std::max<size_t>(count, 1) * sizeof(T);
         b = (b + 255) & ~size_t(255);
-        err = cudaMalloc(&p, b);
+        err = dev_alloc(fault, &p, b);
         if (err != cudaSuccess) return nullptr;
         ptrs.push_back(p);
         bytes += b;
@@ -67,6 +86,7 @@ struct DevMem {
 // Device work arrays for up to pos_cap positions in up to seg_cap segments.
 struct Workspace {
     size_t pos_cap = 0, tile_cap = 0;
+    uint64_t gen = 0;   // bumped by every (re)allocation: a graph captured on older arrays is stale
     Work w{};
     DevMem mem;
 
@@ -120,6 +140,7 @@ struct Workspace {
             w = Work{};
             pos_cap = tile_cap = 0;
         }
+        ++gen;
         return e;
     }
 };
@@ -190,6 +211,7 @@ struct tpc_ctx {
     uint64_t budget = 0;
     int ctas_per_sm = 0;
     int sms = 1;
+    int64_t fail_alloc = 0;        // TPC_OPT_FAIL_ALLOC countdown (0: off)
 
     // non-streaming pending hits
     const tpc_hit *zc = nullptr;   // zero-copy: one device push
@@ -238,7 +260,7 @@ struct tpc_ctx {
     // graph of the step sequence
     cudaGraphExec_t graph = nullptr;
     int graph_nsegs = 0;
-    size_t graph_pos_cap = 0;
+    uint64_t graph_gen = 0;        // workspace generation the graph was captured on
     int graph_grid = 0;
 
     std::mutex mu;
@@ -323,7 +345,7 @@ cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, 
         enqueue_kernels(ws.w, nsegs, Launch{L.grid, st, tr, owner->sms, L.cap});
         return cudaGetLastError();
     }
-    if (!owner->graph || owner->graph_nsegs != nsegs || owner->graph_pos_cap != ws.pos_cap ||
+    if (!owner->graph || owner->graph_nsegs != nsegs || owner->graph_gen != ws.gen ||
         owner->graph_grid != L.grid) {
         if (owner->graph) {
             cudaGraphExecDestroy(owner->graph);
@@ -346,7 +368,7 @@ cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, 
             return e;
         }
         owner->graph_nsegs = nsegs;
-        owner->graph_pos_cap = ws.pos_cap;
+        owner->graph_gen = ws.gen;
         owner->graph_grid = L.grid;
     }
     return cudaGraphLaunch(owner->graph, st);
@@ -369,7 +391,7 @@ cudaError_t stage_host(tpc_ctx *c, tpc_hit *dst, const tpc_hit *src, size_t n) {
     cudaGetLastError();   // clear a possible "not a device pointer" error
     const size_t chunk = size_t(1) << 20;
     if (!c->h_stage) {
-        cudaError_t e = cudaMallocHost(&c->h_stage, chunk * sizeof(tpc_hit));
+        cudaError_t e = host_alloc(&c->fail_alloc, (void **)&c->h_stage, chunk * sizeof(tpc_hit));
         if (e != cudaSuccess) return e;
         c->stage_cap = chunk;
     }
@@ -398,7 +420,7 @@ int materialise(tpc_ctx *c, size_t more) {
         size_t cap = std::max(need, c->in_cap * 2);
         if (over_budget(c, (cap - c->in_cap) * sizeof(tpc_hit))) return TPC_ERR_BUSY;
         tpc_hit *nb = nullptr;
-        if (cudaMalloc(&nb, cap * sizeof(tpc_hit)) != cudaSuccess) return TPC_ERR_NOMEM;
+        if (dev_alloc(&c->fail_alloc, (void **)&nb, cap * sizeof(tpc_hit)) != cudaSuccess) return TPC_ERR_NOMEM;
         const tpc_hit *src = c->zc ? c->zc : c->in;
         if (c->pending &&
             cudaMemcpyAsync(nb, src, c->pending * sizeof(tpc_hit), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
@@ -436,8 +458,8 @@ int ensure_stream_buffers(tpc_ctx *c, size_t chunk) {
     tpc_hit *nb[2] = {nullptr, nullptr};
     uint64_t *ng[2] = {nullptr, nullptr};
     for (int i = 0; i < 2; ++i) {
-        if (cudaMalloc(&nb[i], (ncarry + nchunk) * sizeof(tpc_hit)) != cudaSuccess ||
-            cudaMalloc(&ng[i], (ncarry + nchunk) * sizeof(uint64_t)) != cudaSuccess) {
+        if (dev_alloc(&c->fail_alloc, (void **)&nb[i], (ncarry + nchunk) * sizeof(tpc_hit)) != cudaSuccess ||
+            dev_alloc(&c->fail_alloc, (void **)&ng[i], (ncarry + nchunk) * sizeof(uint64_t)) != cudaSuccess) {
             for (int j = 0; j < 2; ++j) { cudaFree(nb[j]); cudaFree(ng[j]); }
             return TPC_ERR_NOMEM;
         }
@@ -468,6 +490,7 @@ int ensure_stream_buffers(tpc_ctx *c, size_t chunk) {
 int stream_step(tpc_ctx *c, size_t n, bool close_all) {
     const int in = 1 - c->scur;
     const size_t positions = c->carry_ub + n;
+    c->has_result = false;   // the workspace may move: the last result is gone
     if (c->ws.ensure(positions) != cudaSuccess) return TPC_ERR_NOMEM;
     if (ensure_out(c, c->carry_cap + c->chunk_cap) != cudaSuccess) return TPC_ERR_NOMEM;
     Seg s = base_seg(c);
@@ -531,6 +554,7 @@ int tpc_create(uint32_t width, uint32_t height, uint64_t dt, int variant, tpc_ct
     c->dt = dt;
     c->dt32 = dt > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)dt;
     c->variant = variant;
+    c->ws.mem.fault = c->vs.mem.fault = c->outmem.fault = &c->fail_alloc;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return TPC_ERR_CUDA; }
     c->sms = num_sms(c->device);
     if (init_kernel_attributes() != cudaSuccess) { delete c; return TPC_ERR_CUDA; }
@@ -556,13 +580,18 @@ int tpc_set_option(tpc_ctx *c, int key, uint64_t value) {
     case TPC_OPT_MAX_DISORDER:
         if (busy) return TPC_ERR_STATE;
         if (value == 0) return TPC_ERR_ARG;
-        c->max_disorder = value;
-        if (value != ~0ull && !c->ss) {
-            if (cudaMalloc(&c->ss, sizeof(StreamState)) != cudaSuccess) return TPC_ERR_NOMEM;
-            if (cudaMemsetAsync(c->ss, 0, sizeof(StreamState), c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+        if (value != ~0ull && !c->ss) {   // the stream state first: the option stands only with it
+            StreamState *ss = nullptr;
+            if (dev_alloc(&c->fail_alloc, (void **)&ss, sizeof(StreamState)) != cudaSuccess) return TPC_ERR_NOMEM;
+            if (cudaMemsetAsync(ss, 0, sizeof(StreamState), c->stream) != cudaSuccess) {
+                cudaFree(ss);
+                return TPC_ERR_CUDA;
+            }
+            c->ss = ss;
             c->scur = 1;
             c->carry_ub = 0;
         }
+        c->max_disorder = value;
         return TPC_OK;
     case TPC_OPT_MEM_BUDGET:
         c->budget = value;
@@ -582,6 +611,10 @@ int tpc_set_option(tpc_ctx *c, int key, uint64_t value) {
     case TPC_OPT_CTAS_PER_SM:
         if (value > 64) return TPC_ERR_ARG;
         c->ctas_per_sm = (int)value;
+        return TPC_OK;
+    case TPC_OPT_FAIL_ALLOC:
+        if (value > (uint64_t)INT64_MAX) return TPC_ERR_ARG;
+        c->fail_alloc = (int64_t)value;
         return TPC_OK;
     default:
         return TPC_ERR_ARG;
@@ -604,7 +637,7 @@ int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
         cudaError_t e = where == TPC_HOST
             ? stage_host(c, dst, hits, n)
             : cudaMemcpyAsync(dst, hits, n * sizeof(tpc_hit), cudaMemcpyDeviceToDevice, c->stream);
-        if (e != cudaSuccess) return TPC_ERR_CUDA;
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TPC_ERR_NOMEM : TPC_ERR_CUDA;
         return stream_step(c, n, false);
     }
     if (n == 0) return TPC_OK;
@@ -618,7 +651,7 @@ int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
     cudaError_t e = where == TPC_HOST
         ? stage_host(c, c->in + c->pending, hits, n)
         : cudaMemcpyAsync(c->in + c->pending, hits, n * sizeof(tpc_hit), cudaMemcpyDeviceToDevice, c->stream);
-    if (e != cudaSuccess) return TPC_ERR_CUDA;
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TPC_ERR_NOMEM : TPC_ERR_CUDA;
     c->pending += n;
     return TPC_OK;
 }
@@ -628,10 +661,12 @@ int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
 // Launched without a graph; (b) waits for the host between rounds.
 static int flush_variant(tpc_ctx *c, Tracer *tr) {
     const size_t n = c->pending;
+    c->has_result = false;   // the workspace may move: the last result is gone
     if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
     if (c->vs.ensure(c->ws.pos_cap, (size_t)c->width * c->height) != cudaSuccess) return TPC_ERR_NOMEM;
     if (ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
-    if (!c->h_flag && cudaMallocHost(&c->h_flag, sizeof(uint32_t)) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (!c->h_flag && host_alloc(&c->fail_alloc, (void **)&c->h_flag, sizeof(uint32_t)) != cudaSuccess)
+        return TPC_ERR_NOMEM;
     Seg s = base_seg(c);
     s.hits = c->zc ? c->zc : c->in;
     s.out_labels = c->d_labels;
@@ -695,6 +730,7 @@ static int flush_impl(tpc_ctx *c, Tracer *tr) {
     }
     if (c->variant != TPC_LOCAL) return flush_variant(c, tr);
     const size_t n = c->pending;
+    c->has_result = false;   // the workspace may move: the last result is gone
     if (over_budget(c, Workspace::bytes_for(n) > c->ws.mem.bytes ? Workspace::bytes_for(n) - c->ws.mem.bytes : 0))
         return TPC_ERR_BUSY;
     if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
@@ -832,6 +868,7 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
     tpc_ctx *lead = ctxs[0];
     std::vector<std::unique_lock<std::mutex>> locks;
     for (int i = 0; i < n; ++i) locks.emplace_back(ctxs[i]->mu);
+    for (int i = 0; i < n; ++i) ctxs[i]->has_result = false;   // workspaces may move
     size_t positions = 0;
     for (int i = 0; i < n; ++i) positions += ((ctxs[i]->pending + TILE - 1) / TILE) * TILE;
     // every context's pending copies must land before the lead stream reads them
@@ -953,7 +990,7 @@ int tpc_restore(tpc_ctx *c, const void *buf, size_t n) {
         c->carry_ub = 0;
     }
     if (!c->ss) {
-        if (cudaMalloc(&c->ss, sizeof(StreamState)) != cudaSuccess) return TPC_ERR_NOMEM;
+        if (dev_alloc(&c->fail_alloc, (void **)&c->ss, sizeof(StreamState)) != cudaSuccess) return TPC_ERR_NOMEM;
         if (cudaMemsetAsync(c->ss, 0, sizeof(StreamState), c->stream) != cudaSuccess) return TPC_ERR_CUDA;
         c->scur = 1;
         c->carry_ub = 0;
