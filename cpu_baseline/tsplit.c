@@ -554,9 +554,10 @@ int tsplit_cluster(const ts_hit *h, uint64_t n, uint32_t W, uint32_t H, uint64_t
     memset(&J, 0, sizeof(J));
     ts_job *j = &J;
     j->h = h; j->n = n; j->W = W; j->H = H; j->dt = dt; j->toa0 = tmin; j->threads = threads;
-    /* at most about n / 8 windows: a sparse stream gets wider windows */
+    /* at most n / (2 threads) + 1 windows, so that the per-worker window
+       histograms hold at most 2n counters: a sparse stream gets wider windows */
     uint64_t win = window;
-    const uint64_t max_windows = n / 8 + 1;
+    const uint64_t max_windows = n / (2 * (uint64_t)threads) + 1;
     if ((tmax - tmin) / win + 1 > max_windows) win = (tmax - tmin) / max_windows + 1;
     if (win <= dt) win = dt + 1;
     j->window = win;

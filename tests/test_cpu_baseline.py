@@ -59,10 +59,10 @@ def test_track_spanning_many_windows():
     btoa = rng.integers(1000, 1000 + 100 * n, 500).astype(np.uint64)
     hits = oracle.make_hits(np.r_[x, bx], np.r_[y, by], np.r_[toa, btoa], np.r_[np.full(n, 3), np.full(500, 2)])
     perm = rng.permutation(len(hits))
-    casc = same(hits[perm], 256, 256, 128, 129, 4)
-    # 800 hits allow at most 800 / 8 + 1 windows (sparse input widens them):
-    # about 100 borders, each crossed by the track
-    assert casc["merged"] >= 90
+    casc = same(hits[perm], 256, 256, 128, 129, 2)
+    # 800 hits on 2 workers allow at most 800 / 4 + 1 windows (sparse input
+    # widens them): about 200 borders, each crossed by the track
+    assert casc["merged"] >= 150
 
 
 def test_edges():
