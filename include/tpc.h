@@ -186,6 +186,19 @@ int tpc_counts(tpc_ctx *ctx, size_t *n_hits, size_t *n_clusters, size_t *n_open)
    spirit of its wall-clock measurements (Section 4, benchmark set-up). */
 int tpc_profile_flush(tpc_ctx *ctx, const char **names, float *ms, int cap, int *n_out);
 
+/* Diagnostics: the union-find forest of the last processing step of this
+   context (tpc_flush or a streaming push; not a batch), the structure of
+   Section 4.1.  Hits are numbered by position in the step's (ToA, input)
+   order; parent[p] is the position of p's parent (p itself for a root) and
+   input_pos[p] the input index of the hit at position p (0-based within the
+   step: the carried open hits first when streaming, then the new chunk).
+   Both host arrays hold at least cap entries; *n_out = hits in the step;
+   TPC_ERR_CAP if that exceeds cap; TPC_ERR_STATE after a batch or before
+   any step.  Waits for the context's work.  Every parent precedes its child
+   in (ToA, input) order, so toa(parent(h)) <= toa(h), the time invariant of
+   Section 4.1, and each root is its cluster's earliest hit. */
+int tpc_forest(tpc_ctx *ctx, uint32_t *parent, uint32_t *input_pos, size_t cap, size_t *n_out);
+
 /* Bytes of device memory the context currently holds. */
 int tpc_device_bytes(tpc_ctx *ctx, size_t *bytes);
 

@@ -47,6 +47,7 @@ SIGNATURES = {
     "tpc_batch_flush": ([ctypes.POINTER(_VP), _INT], _INT),
     "tpc_counts": ([_VP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)], _INT),
     "tpc_device_bytes": ([_VP, ctypes.POINTER(_SZ)], _INT),
+    "tpc_forest": ([_VP, _VP, _VP, _SZ, ctypes.POINTER(_SZ)], _INT),
     "tpc_profile_flush": ([_VP, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                            _INT, ctypes.POINTER(_INT)], _INT),
     "tpc_snapshot": ([_VP, _VP, _SZ, ctypes.POINTER(_SZ)], _INT),
@@ -266,6 +267,20 @@ class Clusterer:
         buf = ctypes.create_string_buffer(bytes(snap), len(snap))
         _check(self._lib.tpc_restore(self._h, buf, len(snap)), "tpc_restore")
         self._keep.clear()
+
+    def forest(self):
+        """Diagnostics (``tpc_forest``): the last step's union-find forest as
+        (parent, input_pos) uint32 arrays indexed by (ToA, input) position."""
+        n = ctypes.c_size_t()
+        rc = self._lib.tpc_forest(self._h, None, None, 0, ctypes.byref(n))
+        if rc not in (0, -7):   # TPC_ERR_CAP: the size query
+            _check(rc, "tpc_forest")
+        parent = np.empty(n.value, dtype=np.uint32)
+        pos = np.empty(n.value, dtype=np.uint32)
+        _check(self._lib.tpc_forest(self._h, parent.ctypes.data if n.value else None,
+                                    pos.ctypes.data if n.value else None, n.value,
+                                    ctypes.byref(n)), "tpc_forest")
+        return parent, pos
 
     def device_bytes(self) -> int:
         b = ctypes.c_size_t()

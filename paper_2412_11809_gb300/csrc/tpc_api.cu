@@ -916,6 +916,33 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
     return TPC_OK;
 }
 
+int tpc_forest(tpc_ctx *c, uint32_t *parent, uint32_t *input_pos, size_t cap, size_t *n_out) {
+    if (!c || !n_out) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    *n_out = 0;
+    ResultInfo r;
+    int rc = read_result(c, r);
+    if (rc) return rc;
+    if (!c->has_result || c->res_seg != c->ws.w.seg) return TPC_ERR_STATE;
+    const size_t n = r.seg.n;
+    *n_out = n;
+    if (n > cap) return TPC_ERR_CAP;
+    if (!n) return TPC_OK;
+    if (!parent || !input_pos) return TPC_ERR_ARG;
+    // the sorted order lives in the buffer the step's last sort pass wrote
+    const uint32_t sel = r.prob.npasses & 1u;
+    if (cudaMemcpy(parent, c->ws.w.parent + r.seg.off, n * sizeof(uint32_t), cudaMemcpyDeviceToHost) !=
+            cudaSuccess ||
+        cudaMemcpy(input_pos, c->ws.w.vals[sel] + r.seg.off, n * sizeof(uint32_t), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return TPC_ERR_CUDA;
+    for (size_t i = 0; i < n; ++i) {   // positions and input indices relative to the step
+        parent[i] -= r.seg.off;
+        input_pos[i] -= r.seg.off;
+    }
+    return TPC_OK;
+}
+
 int tpc_device_bytes(tpc_ctx *c, size_t *bytes) {
     if (!c || !bytes) return TPC_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
