@@ -288,3 +288,13 @@ def test_wide_span_takes_general_sort():
     hits = hits[np.argsort(hits["toa"], kind="stable")]
     lab, _ = check_against_oracle(hits, 64, 64, 200_000_000)
     assert len(np.unique(lab)) < len(hits)   # clusters did form
+
+
+@pytest.mark.parametrize("cap", [1, 2])
+def test_cta_cap_gives_the_same_result(cap):
+    """TPC_OPT_CTAS_PER_SM caps every persistent grid below its occupancy;
+    each kernel loops over its tiles whatever the grid, so labels and
+    features are unchanged (one-shot (a), and variant (c))."""
+    hits, _ = synth.cfg1(scale=1_500_000 / (64 * 2**20), seed=95)
+    check_against_oracle(hits, 256, 256, 128, ctas_per_sm=cap)
+    check_against_oracle(hits[:200_000], 256, 256, 128, "static", ctas_per_sm=cap)
