@@ -13,6 +13,15 @@ N > 1 runs under torchrun, one independent replica per GPU (the detectors
 are independent; no collective on the data path); value = hits of all ranks
 / max-over-ranks time.  The reference arm (--impl reference) times the CPU
 oracle on the host cores over a bounded sample of the same stream.
+
+Besides value, the JSON line carries: roofline (dominant kernel) and
+path_roofline; kernel_ms (one profiled step); e2e (pinned host buffers in,
+host results out); cpu_baseline (the oracle, one core, a bounded sample);
+cpu_parallel (the paper's temporal-split CPU method on every host core, with
+its merge-cascade counters and thread scaling); clocks; and, unless
+--no-extras, serving (8 streams, latency percentiles), batched (16 detectors
+in one step), large_sensor (448x512, variants a/b/c) and ingest (Algorithm 2
+on the host, alone and feeding a streaming context).
 """
 from __future__ import annotations
 

@@ -1,6 +1,7 @@
 """The multi-process side of bench.py on CPU (gloo, world size 2): ranks
 agree on the slowest rank's time and the whole-job rate counts every rank's
 hits; the reference arm runs on rank 0 only."""
+import json
 import os
 import socket
 import subprocess
@@ -62,3 +63,29 @@ def test_reference_arm_is_rank0_only():
                          timeout=300)
     assert out.returncode == 0
     assert out.stdout.strip() == ""
+
+
+def test_stored_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """A stored ncu traffic figure is used only while the kernel sources hash
+    to the value it was captured with; host-only files do not enter the hash."""
+    import shutil
+    import bench
+    root = tmp_path / "repo"
+    csrc = root / "paper_2412_11809_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = os.path.join(bench.ROOT, "paper_2412_11809_gb300", "csrc")
+    for f in os.listdir(src):
+        if f.endswith((".cu", ".cuh")):
+            shutil.copy(os.path.join(src, f), csrc / f)
+    (root / "profiles").mkdir()
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), root / "profiles" / "traffic.json")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    rec = json.load(open(root / "profiles" / "traffic.json"))["k_tile_link_table"]
+    assert bench.kernel_source_sha() == rec["source_sha"]
+    assert bench.stored_traffic("k_tile_link_table", 1000) == pytest.approx(rec["dram_bytes_per_hit"] * 1000)
+    with open(csrc / "filler.cu", "a") as f:          # host-only code: still valid
+        f.write("\n// host-side change\n")
+    assert bench.stored_traffic("k_tile_link_table", 1000) is not None
+    with open(csrc / "link.cu", "a") as f:            # the kernel changed: no figure
+        f.write("\n// kernel change\n")
+    assert bench.stored_traffic("k_tile_link_table", 1000) is None
