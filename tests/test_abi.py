@@ -58,6 +58,8 @@ def test_checkpoint_argument_checks_without_gpu(lib):
     assert lib.tpc_restore(None, None, 0) == -1
     buf = ctypes.create_string_buffer(64)
     assert lib.tpc_restore(None, buf, 64) == -1
+    assert lib.tpc_forest(None, None, None, 0, ctypes.byref(n)) == -1
+    assert lib.tpc_set_option(None, 5, 1) == -1
 
 
 def test_record_layout_in_c():
