@@ -360,13 +360,15 @@ static void *phase_borders(void *arg) {
         const uint64_t a0 = j->win_start[k], a1 = j->win_start[k + 1], b1 = j->win_start[k + 2];
         if (a0 == a1 || a1 == b1) continue;
         const uint64_t border = j->toa0 + (k + 1) * j->window;
-        /* left slab: ToA >= border - dt (a suffix of window k, ToA ordered) */
+        /* left slab: border - ToA <= dt (a suffix of window k, ToA ordered;
+           its ToAs are below the border) */
         uint64_t ls0 = a1;
-        while (ls0 > a0 && j->g[ls0 - 1].toa + dt >= border) --ls0;
-        /* right slab: ToA <= last ToA of the left window + dt, at most
-           border - 1 + dt (a prefix of window k + 1) */
+        while (ls0 > a0 && border - j->g[ls0 - 1].toa <= dt) --ls0;
+        /* right slab: ToA - border < dt, i.e. within dt of some ToA before the
+           border (a prefix of window k + 1, ToAs at or after the border);
+           written as differences, so ToAs near 2^64 do not wrap */
         uint64_t rs1 = a1;
-        while (rs1 < b1 && j->g[rs1].toa <= border - 1 + dt) ++rs1;
+        while (rs1 < b1 && j->g[rs1].toa - border < dt) ++rs1;
         if (ls0 == a1 || rs1 == a1) continue;
         const int wl = worker_of_window(j, k), wr = worker_of_window(j, k + 1);
         if (slab_clusters(j, ls0, a1, wl, &ls, &nls, &cap_ls, &ll, &cap_ll) ||

@@ -81,6 +81,17 @@ def test_edges():
     assert lab[1] == 0 and lab[3] == 3
 
 
+def test_toa_near_top_of_range():
+    """ToAs within 2^20 ticks of 2^64 and a wide dt: the border slabs are
+    found by differences, nothing wraps."""
+    rng = np.random.default_rng(12)
+    n = 30_000
+    toa = np.uint64(2**64 - 2**20) + rng.integers(0, 2**20 - 1, n).astype(np.uint64)
+    hits = oracle.make_hits(rng.integers(0, 32, n), rng.integers(0, 32, n), toa, rng.integers(1, 50, n))
+    for dt, window in ((20, 200), (5000, 5001), (2**62, 2**62 + 1)):
+        same(hits, 32, 32, dt, window, 3)
+
+
 def test_arguments():
     h = oracle.make_hits([300], [0], [5])
     with pytest.raises(ValueError, match="outside"):
