@@ -102,9 +102,9 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel: str, n_hits: int):
-    """DRAM bytes per launch of `kernel` at n_hits, from profiles/traffic.json
-    (written from an ncu capture of the same sources), else None."""
+def stored_profile(kernel: str, field: str):
+    """A per-hit figure of `kernel` from profiles/traffic.json (written from
+    ncu captures of the same kernel sources), else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel)
@@ -112,7 +112,29 @@ def stored_traffic(kernel: str, n_hits: int):
         return None
     if not rec or rec.get("source_sha") != kernel_source_sha():
         return None
-    return rec["dram_bytes_per_hit"] * n_hits
+    return rec.get(field)
+
+
+def stored_traffic(kernel: str, n_hits: int):
+    """DRAM bytes per launch of `kernel` at n_hits, else None."""
+    per_hit = stored_profile(kernel, "dram_bytes_per_hit")
+    return None if per_hit is None else per_hit * n_hits
+
+
+def issue_roofline(kernel: str, n_hits: int, kernel_ms: float, sms: int, sm_mhz):
+    """Warp instructions issued per second by `kernel` (its stored ncu count
+    per hit x hits / its CUDA-event time) against the SMs' issue limit: four
+    schedulers per SM, one warp instruction each per cycle, at the SM clock
+    sampled during the timed region.  None without a stored count."""
+    per_hit = stored_profile(kernel, "warp_instructions_per_hit")
+    if per_hit is None or not sm_mhz or not kernel_ms:
+        return None
+    achieved = per_hit * n_hits / (kernel_ms / 1e3)
+    peak = sms * 4 * sm_mhz * 1e6
+    return {"bound": "issue", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_hit": per_hit,
+            "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz (sampled)"}
 
 
 def measured_peak_gbs() -> tuple[float, str]:
@@ -651,6 +673,13 @@ def run_gpu(args):
         ingest = extra(run_ingest, hits, t_disorder, dev, torch)
 
     if rank == 0:
+        clock_summary = clocks.summary()
+        try:
+            issue = issue_roofline(dominant, n, prof_ms[dominant],
+                                   torch.cuda.get_device_properties(dev).multi_processor_count,
+                                   clock_summary.get("sm_mhz"))
+        except Exception as e:   # reported, never fatal
+            issue = {"error": f"{type(e).__name__}: {e}"}
         line = {
             "metric": METRIC, "value": value, "unit": "hits/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -666,6 +695,7 @@ def run_gpu(args):
                          "kernel_ms": prof_ms[dominant]},
             "path_roofline": {"bytes_per_hit": b_alg, "achieved": path_gbs, "peak": peak,
                               "unit": "GB/s", "frac": path_gbs / peak},
+            "issue_roofline": issue,
             "kernel_ms": prof_ms,
             "cpu_baseline": cpu,
             "cpu_parallel": cpu_par,
@@ -674,7 +704,7 @@ def run_gpu(args):
                     "pipelining": "three contexts on three CUDA streams, steps in turn",
                     "link_gbs": link},
             "gpu_launches": n_kernels * args.steps,
-            "clocks": clocks.summary(),
+            "clocks": clock_summary,
             "serving": serving,
             "batched": batched,
             "large_sensor": large,

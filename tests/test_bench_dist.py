@@ -89,3 +89,17 @@ def test_stored_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     with open(csrc / "link.cu", "a") as f:            # the kernel changed: no figure
         f.write("\n// kernel change\n")
     assert bench.stored_traffic("k_tile_link_table", 1000) is None
+
+
+def test_issue_roofline_from_stored_instruction_count():
+    """Warp instructions per hit (stored from ncu) x hits / kernel time against
+    4 schedulers per SM at the sampled clock."""
+    import bench
+    per_hit = bench.stored_profile("k_tile_link_table", "warp_instructions_per_hit")
+    assert per_hit == pytest.approx(350029198 / 2**24)
+    r = bench.issue_roofline("k_tile_link_table", 2**26, 2.0, 152, 2000.0)
+    assert r["peak"] == pytest.approx(152 * 4 * 2000e6)
+    assert r["achieved"] == pytest.approx(per_hit * 2**26 / 2e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert bench.issue_roofline("k_tile_link_table", 2**26, 2.0, 152, None) is None
+    assert bench.issue_roofline("k_accumulate", 2**26, 2.0, 152, 2000.0) is None
