@@ -257,7 +257,8 @@ int tpc_restore(tpc_ctx *ctx, const void *buf, size_t n);
    sends the buffer, and the next buffer becomes the current one.  toa_max
    is the largest ToA of the hits taken while a buffer had room, one value
    for the whole stream.  On a t-ordered stream whose closing windows fit in
-   b_t, buffer k holds exactly the hits earlier than its cut toa_max +
+   b_t, and whose buffers take their first b - b_t hits over more than t
+   ticks, buffer k holds exactly the hits earlier than its cut toa_max +
    t_closing, so clusters are split only across a cut, within dt of it; in
    every case the buffers, taken in the order they are sent, form a
    t-ordered stream again.  Buffers keep arrival order inside; the next
