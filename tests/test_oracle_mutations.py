@@ -29,6 +29,17 @@ MISTAKES = {
         "uint64_t f = u.first[r] < u.first[root] ? u.first[r] : u.first[root];",
         "uint64_t f = u.first[r];"),
     "centroid weights missing": ("swx[c] += (uint64_t)h[i].tot * h[i].x;", "swx[c] += (uint64_t)h[i].x;"),
+    "ToA search window one tick short": ("uint64_t t_lo = t >= dt ? t - dt : 0;",
+                                         "uint64_t t_lo = t >= dt ? t - dt + 1 : 0;"),
+    "pixel lists not in ToA order": ("if (ti != tj) return ti < tj ? -1 : 1;", "if (0) return 0;"),
+    "first ToA taken as the largest": ("if (h[i].toa < out[c].first_toa) out[c].first_toa = h[i].toa;",
+                                       "if (h[i].toa > out[c].first_toa || out[c].first_toa == UINT64_MAX) "
+                                       "out[c].first_toa = h[i].toa;"),
+    "centroid y weighted by x": ("swy[c] += (uint64_t)h[i].tot * h[i].y;", "swy[c] += (uint64_t)h[i].tot * h[i].x;"),
+    "cut without the closing slack": ("cut[cur] = sat_add(toa_max, t_closing);   /* sendToDevice(buffer) */",
+                                      "cut[cur] = toa_max;   /* sendToDevice(buffer) */"),
+    "late hits kept in a full buffer": ("            buffer_of[i] = cur + 1;\n            size_next++;",
+                                        "            buffer_of[i] = cur;\n            size_cur++;"),
     "closing time inclusive": ("} else if (toa < sat_add(toa_max, t_closing) && size_cur < b) {",
                                "} else if (toa <= sat_add(toa_max, t_closing) && size_cur < b) {"),
     "toa_max not kept while filling": ("if (toa > toa_max) toa_max = toa;", ";"),
