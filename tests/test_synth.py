@@ -42,3 +42,24 @@ def test_multi_detector_and_serving_shapes():
     streams = synth.cfg3(hits_per_stream=200_000, n_streams=3, seed=1)
     for hits, sizes, t in streams:
         assert sum(sizes) == len(hits) and all(s >= 65536 for s in sizes[:-1])
+
+
+def test_recipe_statistics():
+    """The generator draws what the input recipe states: ToT = min(1023,
+    1 + round(Exp(40))); blobs of 1 + Geometric(0.3) distinct pixels (mean
+    1 + 0.7/0.3 = 3.33) at 1 Mevent/s; a hit rate of 40 Mhits/s for config 1
+    (1 tick = 1.5625 ns)."""
+    import oracle
+    a, _ = synth.generate(256, 256, 400_000, 17, event_rate_hz=1e6, shuffle_window=1)
+    tot = a["tot"].astype(np.float64)
+    assert abs(tot.mean() - 41.0) < 0.5                    # 1 + E[round(Exp(40))] ~ 41
+    assert a["tot"].min() == 1 and a["tot"].max() <= 1023
+    # blobs at 1 Mevent/s on 65536 pixels almost never touch: clusters = blobs
+    lab = oracle.labels(a, 256, 256, 128)
+    sizes = np.bincount(np.unique(lab, return_inverse=True)[1])
+    assert abs(sizes.mean() - (1 + 0.7 / 0.3)) < 0.1
+    span_s = (int(a["toa"].max()) - int(a["toa"].min())) * 1.5625e-9
+    assert abs(len(sizes) / span_s / 1e6 - 1.0) < 0.05     # events per second
+    h, _ = synth.cfg1(scale=1 / 64, seed=3)
+    span_s = (int(h["toa"].max()) - int(h["toa"].min())) * 1.5625e-9
+    assert abs(len(h) / span_s / 40e6 - 1.0) < 0.05        # hits per second
