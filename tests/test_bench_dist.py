@@ -65,6 +65,27 @@ def test_reference_arm_is_rank0_only():
     assert out.stdout.strip() == ""
 
 
+def test_reference_arm_line():
+    """Rank 0 of the reference arm times the oracle and prints one line with
+    the contract's keys: impl, the same metric and unit, cpu_baseline of kind
+    oracle, and an e2e object with no host-device bytes."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--scale", "0.002", "--ref-sample", "20000", "--steps", "2",
+                          "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    import bench
+    assert rec["impl"] == "reference" and rec["metric"] == bench.METRIC
+    assert rec["unit"] == "hits/s" and rec["higher_is_better"] is True
+    assert rec["steps"] == 2 and rec["warmup"] == 3 and rec["value"] > 0
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["value"] == rec["value"]
+    assert rec["e2e"] == {"value": rec["value"], "unit": "hits/s", "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
+
+
 def test_stored_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     """A stored ncu traffic figure is used only while the kernel sources hash
     to the value it was captured with; host-only files do not enter the hash."""
