@@ -15,7 +15,7 @@ are independent; no collective on the data path); value = hits of all ranks
 oracle on the host cores over a bounded sample of the same stream.
 
 Besides value, the JSON line carries: roofline (dominant kernel) and
-path_roofline; kernel_ms (one profiled step); e2e (pinned host buffers in,
+kernel_roofline; kernel_ms (one profiled step); e2e (pinned host buffers in,
 host results out); cpu_baseline (the oracle, one core, a bounded sample);
 cpu_parallel (the paper's temporal-split CPU method on every host core, with
 its merge-cascade counters and thread scaling); clocks; and, unless
@@ -113,6 +113,14 @@ def stored_profile(kernel: str, field: str):
     if not rec or rec.get("source_sha") != kernel_source_sha():
         return None
     return rec.get(field)
+
+
+def stored_step_traffic(n_hits: int):
+    """DRAM bytes of one whole step at n_hits: the per-hit figures of every
+    kernel of the step in profiles/traffic.json (its "step" record, captured
+    from one ncu launch list of the same kernel sources), else None."""
+    per_hit = stored_profile("step", "dram_bytes_per_hit")
+    return None if per_hit is None else per_hit * n_hits
 
 
 def stored_traffic(kernel: str, n_hits: int):
@@ -249,10 +257,11 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_sample(hits, n_sample: int):
-    """Time the CPU oracle (labels + features) on the first n_sample hits."""
+def oracle_sample(hits, n_sample: int, start: int = 0):
+    """Time the CPU oracle (labels + features) on n_sample consecutive hits
+    starting at `start`."""
     import oracle
-    sub = np.ascontiguousarray(hits[:n_sample])
+    sub = np.ascontiguousarray(hits[start:start + n_sample])
     t0 = time.perf_counter()
     lab = oracle.labels(sub, W, H, DT)
     oracle.features(sub, lab)
@@ -292,24 +301,36 @@ def cpu_parallel_sample(hits, window=6400):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the host cores.
+    The whole 64 Mi-hit stream takes the single-threaded oracle about 47 s,
+    so each step clusters one consecutive slice of --ref-sample hits, step k
+    taking slice k (cycling), so that the steps together walk the stream."""
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
     import synth
     hits, _ = synth.cfg1(scale=args.scale)
     n_sample = min(len(hits), args.ref_sample)
-    for _ in range(args.warmup):
-        oracle_sample(hits, n_sample)
-    times = [oracle_sample(hits, n_sample) for _ in range(args.steps)]
+    n_slices = max(1, len(hits) // n_sample)
+    for k in range(args.warmup):
+        oracle_sample(hits, n_sample, (k % n_slices) * n_sample)
+    times = [oracle_sample(hits, n_sample, (k % n_slices) * n_sample) for k in range(args.steps)]
     total = sum(times)
     value = n_sample * args.steps / total
-    sample = f"first {n_sample} hits of the stream per step (labels + features), single thread"
+    sample = (f"{n_sample} consecutive hits per step, step k taking slice k of the "
+              f"{len(hits)}-hit stream ({min(args.steps, n_slices)} of {n_slices} slices timed); "
+              f"labels + features, single thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "hits/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded generator)",
-        "config": {"workload": WORKLOAD, "n_hits": n_sample, "seed": 1000},
+        "config": {"workload": WORKLOAD, "n_hits": n_sample, "stream_hits": len(hits), "seed": 1000,
+                   "same_config": False,
+                   "why_sampled": (f"the oracle clusters about 1.4 Mhits/s on one core, so one "
+                                   f"{len(hits)}-hit step would take about "
+                                   f"{len(hits) / 1.4e6:.0f} s and {args.steps + args.warmup} steps "
+                                   f"far more than the few minutes the run may take")},
         "cpu_baseline": {"value": value, "unit": "hits/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "hits/s", "h2d_bytes_per_step": 0,
@@ -584,6 +605,7 @@ def run_gpu(args):
     achieved = dom_bytes / (prof_ms[dominant] / 1e3) / 1e9
     b_alg = path_bytes_per_hit(n, n_clusters)
     path_gbs = value / world * b_alg / 1e9
+    step_traffic = stored_step_traffic(n)
 
     # end to end: pinned host input, host results, through the same API.
     # NCTX contexts on their own CUDA streams take the steps in turn, so
@@ -608,7 +630,7 @@ def run_gpu(args):
     def finish(k):
         return ctxs[k % NCTX].features_into(pin_rec[k % NCTX].data_ptr(), rec_cap, device=False)
 
-    e2e_steps = max(NCTX, min(args.steps, 12))
+    e2e_steps = max(NCTX, args.steps)
     for k in range(max(NCTX, args.warmup)):
         issue(k)
         finish(k)
@@ -688,13 +710,23 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "n_hits_per_gpu": n, "clusters": n_clusters,
                        "seed": 1000, "l2": "inputs larger than L2 (1 GiB per step)",
                        "parallelism": f"replicas x{world}", "paper_context": PAPER_CONTEXT},
-            "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
-                         "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": stored_traffic(dominant, n),
-                         "bytes_per_hit": KERNEL_BYTES_PER_HIT.get(dominant, 0),
-                         "kernel_ms": prof_ms[dominant]},
-            "path_roofline": {"bytes_per_hit": b_alg, "achieved": path_gbs, "peak": peak,
-                              "unit": "GB/s", "frac": path_gbs / peak},
+            "roofline": {"bound": "hbm", "achieved": path_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": path_gbs / peak, "traffic": step_traffic,
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                         "bytes_per_hit": b_alg,
+                         "basis": "whole path: hits/s x B_alg, B_alg = 16 B record in + 8 B label out "
+                                  "+ 40 B per cluster record",
+                         "traffic_basis": "sum over the step's kernels of ncu dram__bytes_read.sum + "
+                                          "dram__bytes_write.sum per hit (profiles/traffic.json), x hits",
+                         "traffic_over_alg": (step_traffic / (b_alg * n)) if step_traffic else None},
+            "kernel_roofline": {"bound": "hbm", "kernel": dominant, "kernel_ms": prof_ms[dominant],
+                                "achieved": b_alg * n / (prof_ms[dominant] / 1e3) / 1e9,
+                                "peak": peak, "unit": "GB/s",
+                                "frac": b_alg * n / (prof_ms[dominant] / 1e3) / 1e9 / peak,
+                                "basis": "B_alg x hits of one launch / the dominant kernel's CUDA-event time",
+                                "own_bytes_per_hit": KERNEL_BYTES_PER_HIT.get(dominant, 0),
+                                "own_achieved": achieved, "own_frac": achieved / peak,
+                                "traffic": stored_traffic(dominant, n)},
             "issue_roofline": issue,
             "kernel_ms": prof_ms,
             "cpu_baseline": cpu,

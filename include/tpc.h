@@ -303,29 +303,37 @@ void tpc_filler_destroy(tpc_filler *f);
 /* Largest batch tpc_cluster_static() accepts. */
 #define TPC_STATIC_MAX_HITS 65536
 
+/* Error bits tpc_cluster_static() writes to counts[1] (0 = none). */
+#define TPC_STATIC_E_RANGE 1u   /* a hit outside the sensor (its pixel is clamped) */
+#define TPC_STATIC_E_SPAN 2u    /* the batch's ToA span is 2^32 ticks or more */
+#define TPC_STATIC_E_CAP 16u    /* more clusters than record_cap (> 0): records truncated */
+
 /* One-shot clustering (variant TPC_LOCAL) of at most TPC_STATIC_MAX_HITS
-   hits that allocates nothing, for callers that cannot call cudaMalloc —
-   code running while a stream is captured into a CUDA graph, or real-time
-   readout loops that must not block on the allocator.  The paper has no
-   counterpart; it is an addition of this library.
+   hits that allocates nothing.  The paper has no counterpart; it is an
+   addition of this library, for callers that cannot call cudaMalloc:
+   real-time readout loops that must not block (cudaMalloc can synchronise
+   the device), and code under a fixed memory plan that may only use
+   buffers it was given.
      hits        device pointer, n records (same layout as tpc_push)
      labels      device pointer, n entries: labels[i] = smallest index i'
                  in hit i's cluster (indices 0..n-1 of this call)
      records     device pointer, record_cap cluster records ordered by label
                  (as tpc_cluster_features); may be NULL if record_cap == 0
      counts      device pointer, 2 entries written by the call:
-                 counts[0] = number of clusters, counts[1] = device error
-                 bits (0 = none; non-zero: a hit outside the sensor, a ToA
-                 span of 2^32 ticks or more, or more clusters than
-                 record_cap — records are then truncated)
+                 counts[0] = number of clusters, counts[1] = TPC_STATIC_E_*
+                 bits (0 = none).  With record_cap == 0 (labels only) the
+                 cap bit is never set; with 0 < record_cap < counts[0] it is,
+                 and the first record_cap records are written.
      stream      cudaStream_t (as void *) the work is queued on; 0 = legacy
    Asynchronous: returns after queueing.  TPC_ERR_ARG for n >
    TPC_STATIC_MAX_HITS, null pointers or a sensor larger than tpc_create
    allows.  Working memory is one fixed device array of the library
    (about 4.5 MB per GPU that loads it, held until exit), shared by every
-   call: calls whose work overlaps on the GPU race on it, so order them on
-   one stream.  The first call on a device looks up that array's address
-   and sets kernel attributes; make it before any stream capture. */
+   call and keeping the last call's contents: calls whose work overlaps on
+   the GPU race on it, so order them on one stream.  The first call on a
+   device does set-up (looks up that array's device address with
+   cudaGetSymbolAddress and sets kernel attributes); make that first call
+   before any stream capture. */
 int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width, uint32_t height,
                        uint64_t dt, uint64_t *labels, tpc_cluster *records, size_t record_cap,
                        uint64_t *counts, void *stream);

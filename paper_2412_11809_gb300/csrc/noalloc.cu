@@ -1,12 +1,13 @@
 // tpc_cluster_static: one-shot clustering of a small batch of hits that
 // allocates nothing.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation is not a capturable operation),
-// and real-time readout loops that must not block, since cudaMalloc can
-// synchronise the device.  They hand over device buffers for the inputs and
-// outputs; the working memory comes from the fixed array below, which every
-// GPU that loads the library holds until the process exits.
+// Some callers cannot call cudaMalloc: real-time readout loops that must not
+// block (cudaMalloc can synchronise the device and take unbounded time), and
+// code that runs under a fixed memory plan, such as a host framework that
+// reserved the device memory up front and hands out only buffers from its
+// own pool.  They hand over device buffers for the inputs and outputs; the
+// working memory comes from the fixed array below, which every GPU that
+// loads the library holds until the process exits.
 //
 // The kernels are the library's own (the same launch sequence as
 // tpc_flush); only the source of their scratch differs.  Every call shares
@@ -101,9 +102,12 @@ __global__ void k_na_begin(Work w, Seg s, uint32_t tile_cap, uint32_t pos_cap) {
     *w.prob = p;
 }
 
-__global__ void k_na_end(Work w, uint64_t *counts) {
+// counts[1] keeps the public bits only (TPC_STATIC_E_*); with no record
+// buffer (record_cap == 0) the caller asked for labels alone, so more
+// clusters than records is not an error then.
+__global__ void k_na_end(Work w, uint64_t *counts, uint32_t keep) {
     counts[0] = w.seg[0].n_clusters;
-    counts[1] = w.prob->err;
+    counts[1] = w.prob->err & keep;
 }
 
 __global__ void k_na_empty(uint64_t *counts) {
@@ -183,6 +187,9 @@ extern "C" int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width,
     launch_link(w, L);
     launch_features(w, L);
     launch_outputs(w, L);
-    k_na_end<<<1, 1, 0, st>>>(w, counts);
+    static_assert(E_RANGE == TPC_STATIC_E_RANGE && E_SPAN == TPC_STATIC_E_SPAN && E_CAP == TPC_STATIC_E_CAP,
+                  "public error bits");
+    const uint32_t keep = TPC_STATIC_E_RANGE | TPC_STATIC_E_SPAN | (record_cap ? TPC_STATIC_E_CAP : 0u);
+    k_na_end<<<1, 1, 0, st>>>(w, counts, keep);
     return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }

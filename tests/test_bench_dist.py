@@ -86,9 +86,8 @@ def test_reference_arm_line():
                           "d2h_bytes_per_step": 0}
 
 
-def test_stored_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
-    """A stored ncu traffic figure is used only while the kernel sources hash
-    to the value it was captured with; host-only files do not enter the hash."""
+def _tree_with_profile(tmp_path, monkeypatch, fields):
+    """A copy of the kernel sources with a traffic.json captured "on" them."""
     import shutil
     import bench
     root = tmp_path / "repo"
@@ -99,25 +98,39 @@ def test_stored_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
         if f.endswith((".cu", ".cuh")):
             shutil.copy(os.path.join(src, f), csrc / f)
     (root / "profiles").mkdir()
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), root / "profiles" / "traffic.json")
     monkeypatch.setattr(bench, "ROOT", str(root))
-    rec = json.load(open(root / "profiles" / "traffic.json"))["k_tile_link_table"]
-    assert bench.kernel_source_sha() == rec["source_sha"]
-    assert bench.stored_traffic("k_tile_link_table", 1000) == pytest.approx(rec["dram_bytes_per_hit"] * 1000)
+    rec = {k: dict(v, source_sha=bench.kernel_source_sha()) for k, v in fields.items()}
+    with open(root / "profiles" / "traffic.json", "w") as f:
+        json.dump(rec, f)
+    return root, csrc
+
+
+def test_stored_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """A stored ncu traffic figure is used only while the kernel sources hash
+    to the value it was captured with; host-only files do not enter the hash."""
+    import bench
+    root, csrc = _tree_with_profile(tmp_path, monkeypatch, {
+        "k_tile_link_table": {"dram_bytes_per_hit": 16.0},
+        "step": {"dram_bytes_per_hit": 70.0}})
+    assert bench.stored_traffic("k_tile_link_table", 1000) == pytest.approx(16.0 * 1000)
+    assert bench.stored_step_traffic(1000) == pytest.approx(70.0 * 1000)
     with open(csrc / "filler.cu", "a") as f:          # host-only code: still valid
         f.write("\n// host-side change\n")
     assert bench.stored_traffic("k_tile_link_table", 1000) is not None
     with open(csrc / "link.cu", "a") as f:            # the kernel changed: no figure
         f.write("\n// kernel change\n")
     assert bench.stored_traffic("k_tile_link_table", 1000) is None
+    assert bench.stored_step_traffic(1000) is None
 
 
-def test_issue_roofline_from_stored_instruction_count():
+def test_issue_roofline_from_stored_instruction_count(tmp_path, monkeypatch):
     """Warp instructions per hit (stored from ncu) x hits / kernel time against
     4 schedulers per SM at the sampled clock."""
     import bench
+    _tree_with_profile(tmp_path, monkeypatch, {
+        "k_tile_link_table": {"warp_instructions_per_hit": 20.5}})
     per_hit = bench.stored_profile("k_tile_link_table", "warp_instructions_per_hit")
-    assert per_hit == pytest.approx(350029198 / 2**24)
+    assert per_hit == pytest.approx(20.5)
     r = bench.issue_roofline("k_tile_link_table", 2**26, 2.0, 152, 2000.0)
     assert r["peak"] == pytest.approx(152 * 4 * 2000e6)
     assert r["achieved"] == pytest.approx(per_hit * 2**26 / 2e-3)

@@ -63,3 +63,21 @@ def test_recipe_statistics():
     h, _ = synth.cfg1(scale=1 / 64, seed=3)
     span_s = (int(h["toa"].max()) - int(h["toa"].min())) * 1.5625e-9
     assert abs(len(h) / span_s / 40e6 - 1.0) < 0.05        # hits per second
+
+
+def test_blocked_generation_is_one_t_ordered_stream():
+    """The full-size 448x512 stream is drawn as consecutive sub-streams in
+    parallel: deterministic, t-ordered with the reported t, blocks in time
+    order with a quiet gap longer than any ToT between them."""
+    a, ta = synth.cfg4(scale=1 / 2048, seed=7, blocks=4)
+    b, tb = synth.cfg4(scale=1 / 2048, seed=7, blocks=4)
+    assert ta == tb and np.array_equal(a, b)
+    assert len(a) == 512 * 2**20 // 2048
+    toa = a["toa"].astype(np.int64)
+    run_max = np.maximum.accumulate(toa)
+    assert ta == max(1, int((run_max[:-1] - toa[1:]).max()) + 1)
+    sizes = [len(a) // 4] * 4
+    edges = np.cumsum(sizes)[:-1]
+    for e in edges:   # every hit of a block precedes every hit of the next
+        assert toa[:e].max() + 1024 < toa[e:].min()
+    assert a["x"].max() < 448 and a["y"].max() < 512 and a["tot"].max() <= 1023

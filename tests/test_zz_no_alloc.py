@@ -1,18 +1,22 @@
 """tpc_cluster_static — the entry point that allocates nothing.
 
-Some callers cannot call cudaMalloc (code running inside a CUDA-graph stream
-capture, real-time readout loops that must not block on the allocator).
-This test calls the entry point through the C ABI twice in a row on the
-same inputs and checks both results against the regular context path
-(tpc_push + tpc_flush + tpc_labels / tpc_cluster_features): labels exact,
-integer features exact, centroids within 1e-5 relative.  It lives in a file
-of its own that pytest collects last.
+Some callers cannot call cudaMalloc: real-time readout loops that must not
+block (cudaMalloc can synchronise the device), and code under a fixed memory
+plan that may only use the buffers it was given.  This test calls the entry
+point through the C ABI twice in a row on the same inputs and checks both
+results against the oracle (labels bit-exact, integer features exact,
+centroids within 1e-5 relative) and against the regular context path
+(tpc_push + tpc_flush + tpc_labels / tpc_cluster_features), checks the
+documented error bits for a record buffer smaller than the cluster count and
+for a labels-only call, and that the device's free memory does not change
+across the calls.  It lives in a file of its own that pytest collects last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -22,52 +26,119 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2412_11809_gb300 import CLUSTER_DTYPE, Clusterer, binding  # noqa: E402
+from gpu_helpers import assert_features_equal  # noqa: E402
 
 MAX_HITS = 65536
+E_RANGE, E_SPAN, E_CAP = 1, 2, 16   # TPC_STATIC_E_* of include/tpc.h
 
 
-def _reference(hits, w, h, dt):
+def _context_path(hits, w, h, dt):
     with Clusterer(w, h, dt) as c:
         c.push(hits)
         c.flush()
         return c.labels(), c.features()
 
 
-@pytest.mark.parametrize("sensor", ["256x256", "448x512"])
-def test_static_entry_matches_context_path_twice(sensor):
-    lib = binding.load_library()
+def _inputs(sensor):
     if sensor == "256x256":
-        w, h = 256, 256
         hits, _ = synth.cfg1(scale=60000 / (64 * 2**20), seed=31)   # 60000 hits: 15 tiles, ragged tail
-    else:   # larger than the shared-memory pixel table: linked band by band
-        w, h = 448, 512
-        hits, _ = synth.cfg4(scale=60000 / (512 * 2**20), seed=32)
+        return hits, 256, 256
+    # larger than the shared-memory pixel table: linked band by band
+    hits, _ = synth.cfg4(scale=60000 / (512 * 2**20), seed=32)
+    return hits, 448, 512
+
+
+def _call(lib, d_hits, n, w, h, dt, record_cap, stream):
+    d_lab = torch.full((max(n, 1),), -1, dtype=torch.int64, device="cuda")
+    d_rec = torch.zeros((max(record_cap, 1), CLUSTER_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+    d_cnt = torch.full((2,), -1, dtype=torch.int64, device="cuda")
+    rc = lib.tpc_cluster_static(d_hits.data_ptr(), n, w, h, dt, d_lab.data_ptr(),
+                                d_rec.data_ptr() if record_cap else None, record_cap,
+                                d_cnt.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+    assert rc == 0, binding.STATUS.get(rc, rc)
+    return d_lab, d_rec, d_cnt
+
+
+@pytest.mark.parametrize("sensor", ["256x256", "448x512"])
+def test_static_entry_matches_oracle_twice(sensor):
+    lib = binding.load_library()
+    hits, w, h = _inputs(sensor)
     n = len(hits)
     assert 4096 * 14 < n <= MAX_HITS
-    want_lab, want_rec = _reference(hits, w, h, 128)
+    want_lab = oracle.labels(hits, w, h, 128)
+    want_rec = oracle.features(hits, want_lab)
+    ctx_lab, ctx_rec = _context_path(hits, w, h, 128)
 
     d_hits = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).cuda()
     stream = torch.cuda.current_stream()
-    for call in range(2):
+    _call(lib, d_hits, n, w, h, 128, n, stream)   # warm-up: first-call set-up, module loading
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    torch_alloc0 = torch.cuda.memory_allocated()
+    outs = []
+    for call in range(2):   # buffers made before the calls: the calls themselves allocate nothing
         d_lab = torch.full((n,), -1, dtype=torch.int64, device="cuda")
         d_rec = torch.zeros((n, CLUSTER_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
         d_cnt = torch.full((2,), -1, dtype=torch.int64, device="cuda")
+        outs.append((d_lab, d_rec, d_cnt))
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    torch_alloc1 = torch.cuda.memory_allocated()
+    for d_lab, d_rec, d_cnt in outs:
         rc = lib.tpc_cluster_static(d_hits.data_ptr(), n, w, h, 128, d_lab.data_ptr(),
                                     d_rec.data_ptr(), n, d_cnt.data_ptr(),
                                     ctypes.c_void_p(stream.cuda_stream))
         assert rc == 0, binding.STATUS.get(rc, rc)
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free1, "device free memory changed across the calls"
+    assert torch.cuda.memory_allocated() == torch_alloc1
+    assert free0 >= free1 and torch_alloc1 >= torch_alloc0
+    for call, (d_lab, d_rec, d_cnt) in enumerate(outs):
         n_clusters, err = (int(v) for v in d_cnt.cpu().numpy())
         assert err == 0, f"call {call}: device error bits {err}"
         assert n_clusters == len(want_rec)
         lab = d_lab.cpu().numpy().view(np.uint64)
-        np.testing.assert_array_equal(lab, want_lab, err_msg=f"call {call}")
+        np.testing.assert_array_equal(lab, want_lab, err_msg=f"call {call} vs oracle")
+        np.testing.assert_array_equal(lab, ctx_lab, err_msg=f"call {call} vs context path")
         rec = d_rec.cpu().numpy().view(CLUSTER_DTYPE).reshape(-1)[:n_clusters]
-        for k in ("label", "size", "sum_tot", "first_toa"):
-            np.testing.assert_array_equal(rec[k], want_rec[k], err_msg=f"call {call} {k}")
-        for k in ("cx", "cy"):
-            np.testing.assert_allclose(rec[k], want_rec[k], rtol=1e-5, atol=0,
-                                       err_msg=f"call {call} {k}")
+        assert_features_equal(rec, want_rec)
+        for k in CLUSTER_DTYPE.names:
+            np.testing.assert_array_equal(rec[k], ctx_rec[k], err_msg=f"call {call} {k} vs context path")
+
+
+def test_static_entry_record_cap_and_labels_only():
+    lib = binding.load_library()
+    hits, w, h = _inputs("256x256")
+    n = len(hits)
+    want_lab = oracle.labels(hits, w, h, 128)
+    want_rec = oracle.features(hits, want_lab)
+    d_hits = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).cuda()
+    stream = torch.cuda.current_stream()
+    # fewer records than clusters: the cap bit, the first record_cap records written
+    cap = len(want_rec) // 3
+    d_lab, d_rec, d_cnt = _call(lib, d_hits, n, w, h, 128, cap, stream)
+    torch.cuda.synchronize()
+    n_clusters, err = (int(v) for v in d_cnt.cpu().numpy())
+    assert n_clusters == len(want_rec) and err == E_CAP
+    np.testing.assert_array_equal(d_lab.cpu().numpy().view(np.uint64), want_lab)
+    assert_features_equal(d_rec.cpu().numpy().view(CLUSTER_DTYPE).reshape(-1)[:cap], want_rec[:cap])
+    # labels only: no record buffer, no error bit
+    d_lab, _, d_cnt = _call(lib, d_hits, n, w, h, 128, 0, stream)
+    torch.cuda.synchronize()
+    n_clusters, err = (int(v) for v in d_cnt.cpu().numpy())
+    assert n_clusters == len(want_rec) and err == 0
+    np.testing.assert_array_equal(d_lab.cpu().numpy().view(np.uint64), want_lab)
+
+
+def test_static_entry_reports_out_of_range_hit():
+    lib = binding.load_library()
+    hits, w, h = _inputs("256x256")
+    hits = hits[:5000].copy()
+    hits["x"][1234] = 300          # outside the 256-wide sensor: reported, not read out of bounds
+    d_hits = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).cuda()
+    _, _, d_cnt = _call(lib, d_hits, len(hits), w, h, 128, len(hits), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert int(d_cnt.cpu().numpy()[1]) & E_RANGE
 
 
 def test_static_entry_rejects_oversize_batch():
