@@ -341,99 +341,167 @@ def run_reference(args):
 
 
 def run_serving(args, dev, torch):
-    """8 streams, chunks log-uniform in [64k, 2M] hits, each stream's base
-    stream replayed with a ToA offset (as the paper repeats its data, Section 4)
-    until enough chunks; one host thread and one CUDA stream per detector.
-    Latency per chunk: push (H2D from pinned memory) to labels and records of
-    the finalised clusters back on the host."""
+    """Config 3 through the serving loop (tpc_server_*): 8 streams of 50
+    Mhits/s (400 Mhits/s offered in all), each cut into chunks log-uniform in
+    [64k, 2M] hits; each stream's base stream is replayed with a ToA offset
+    (as the paper repeats its data, Section 4) until enough chunks.  Open
+    loop: chunk j of a stream is submitted when its last hit has arrived at
+    the stream's rate (pinned host buffers), whatever the state of the GPU;
+    a waiter thread collects the results.  Latency per chunk: submission to
+    finalised labels, indices and records in host memory, queueing included.
+    Then the same chunks submitted all at once (flat out) for the serving
+    throughput limit."""
     import threading
     import synth
-    from paper_2412_11809_gb300 import CLUSTER_DTYPE, Clusterer
-    streams = synth.cfg3(hits_per_stream=args.serving_hits, n_streams=8, seed=3000)
-    reps = max(1, -(-args.serving_chunks // sum(len(s[1]) for s in streams)))
-    lat, straddle = [[] for _ in streams], []
-    totals = [0] * len(streams)
-    errors = []
-
-    def worker(i):
-        try:
-            hits, sizes, t = streams[i]
-            span = int(hits["toa"].max() - hits["toa"].min()) + 10 * 128
-            ctx = Clusterer(W, H, DT, max_disorder=t, stream=torch.cuda.Stream(device=dev))
-            cap = 2 * max(sizes) + 1_000_000
-            pin_lab = torch.empty(cap, dtype=torch.int64).pin_memory()
-            pin_idx = torch.empty(cap, dtype=torch.int64).pin_memory()
-            pin_rec = torch.empty((cap, CLUSTER_DTYPE.itemsize), dtype=torch.uint8).pin_memory()
-            chunks = []
+    from paper_2412_11809_gb300 import CLUSTER_DTYPE, Server
+    rate = 50e6
+    streams = synth.cfg3(hits_per_stream=args.serving_hits, n_streams=8, seed=3000, rate_hz=rate)
+    per_stream = max(1, args.serving_chunks // len(streams))
+    plans = []   # per stream: list of (host tensor of the chunk, n)
+    first_rep = []
+    for hits, sizes, t in streams:
+        span = int(hits["toa"].max() - hits["toa"].min()) + 10 * DT
+        chunks, rep = [], 0
+        while len(chunks) < per_stream:
+            copy = hits.copy()
+            copy["toa"] += np.uint64(rep * span)
+            pinned = torch.from_numpy(copy.view(np.uint8).reshape(-1, 16)).pin_memory()
             start = 0
-            for s in sizes:
-                chunks.append(torch.from_numpy(hits[start:start + s].view(np.uint8).reshape(-1, 16)).pin_memory())
-                start += s
-            first_lab, first_idx = [], []
-            for r in range(reps):
-                for k, ch in enumerate(chunks):
-                    if r:   # replay with a ToA offset: a later, t-ordered continuation
-                        view = ch.numpy().view(HIT_DTYPE_NP).reshape(-1)
-                        view["toa"] += np.uint64(span)
-                    t0 = time.perf_counter()
-                    ctx.push_ptr(ch.data_ptr(), ch.shape[0], device=False)
-                    m = ctx.labels_into(pin_lab.data_ptr(), cap, device=False, indices_ptr=pin_idx.data_ptr())
-                    ctx.features_into(pin_rec.data_ptr(), cap, device=False)
-                    lat[i].append(time.perf_counter() - t0)
-                    totals[i] += ch.shape[0]
-                    if r == 0:
-                        first_lab.append(pin_lab[:m].numpy().copy())
-                        first_idx.append(pin_idx[:m].numpy().copy())
-            ctx.flush()
-            ctx.sync()
-            ctx.close()
-            if first_lab:
-                lab = np.concatenate(first_lab)
-                idx = np.concatenate(first_idx)
-                chunk_of = np.searchsorted(np.cumsum(sizes), idx, side="right")
-                lab_chunk = np.searchsorted(np.cumsum(sizes), lab, side="right")
-                crossing = np.unique(lab[chunk_of != lab_chunk])
-                straddle.append(len(crossing) / max(1, len(np.unique(lab))))
-        except Exception as e:   # reported in the JSON line
-            errors.append(repr(e))
+            for n in sizes:
+                chunks.append((pinned[start:start + n], n))
+                start += n
+                if len(chunks) >= per_stream:
+                    break
+            rep += 1
+        plans.append(chunks)
+        first_rep.append(sizes)
+    cap = max(n for pl in plans for _, n in pl) + (1 << 20)
 
-    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(streams))]
-    t0 = time.perf_counter()
-    for th in threads:
+    def run(budget, open_loop):
+        results = []
+        srv = Server(budget)
+        ids = [srv.add_stream(W, H, DT, t) for _, _, t in streams]
+        slots = {}   # tag -> (labels, indices, records) pinned outputs
+        events = []  # (arrival time offset s, stream, chunk index)
+        for k, pl in enumerate(plans):
+            acc = 0
+            for j, (_, n) in enumerate(pl):
+                acc += n
+                events.append((acc / rate if open_loop else 0.0, k, j))
+        events.sort()
+        free_out = [(torch.empty(cap, dtype=torch.int64).pin_memory(),
+                     torch.empty(cap, dtype=torch.int64).pin_memory(),
+                     torch.empty((cap, CLUSTER_DTYPE.itemsize), dtype=torch.uint8).pin_memory())
+                    for _ in range(16)]
+        lock = threading.Condition()
+        done_first = {}   # (stream, j) -> (indices, labels) of the first replay, for the straddle count
+
+        def waiter():
+            for _ in range(len(events)):
+                r = srv.wait_raw(timeout_s=300)
+                if r is None:
+                    results.append(None)
+                    return
+                k, j = divmod(r.tag, 1 << 20)
+                lab, idx, rec = slots.pop(r.tag)
+                if j < len(first_rep[k]) and r.status == 0:
+                    done_first[(k, j)] = (idx[:r.n_hits].numpy().copy(), lab[:r.n_hits].numpy().copy())
+                results.append((r.status, r.n_hits, r.queue_ms, r.latency_ms))
+                with lock:
+                    free_out.append((lab, idx, rec))
+                    lock.notify()
+
+        th = threading.Thread(target=waiter)
         th.start()
-    for th in threads:
+        t0 = time.perf_counter()
+        for when, k, j in events:
+            delay = t0 + when - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            with lock:
+                while not free_out:
+                    lock.wait()
+                lab, idx, rec = free_out.pop()
+            tag = k * (1 << 20) + j
+            slots[tag] = (lab, idx, rec)
+            chunk, n = plans[k][j]
+            srv.submit_ptr(ids[k], chunk.data_ptr(), n, lab.data_ptr(), idx.data_ptr(), rec.data_ptr(),
+                           cap, tag)
         th.join()
-    wall = time.perf_counter() - t0
-    all_lat = np.array([v for l in lat for v in l]) * 1e3
-    out = {"streams": len(streams), "chunks": int(len(all_lat)), "chunk_hits": "log-uniform 64k-2M",
-           "hits_per_s": sum(totals) / wall if wall > 0 else None,
-           "p50_ms": float(np.percentile(all_lat, 50)) if len(all_lat) else None,
-           "p99_ms": float(np.percentile(all_lat, 99)) if len(all_lat) else None,
-           "straddling_cluster_frac": float(np.mean(straddle)) if straddle else None,
-           "latency": "host push (pinned H2D) to finalised labels+records on host, per chunk"}
-    if errors:
-        out["errors"] = errors[:3]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return results, wall, st, done_first
+
+    budget = args.serving_budget
+    out = {"streams": len(streams), "chunk_hits": "log-uniform 64k-2M", "budget_bytes": budget,
+           "latency": "submission (at the chunk's arrival) to finalised labels, indices and records "
+                      "in pinned host memory, queueing included"}
+    for name, open_loop in (("offered_400mhits", True), ("flat_out", False)):
+        res, wall, st, first = run(budget, open_loop)
+        ok = [r for r in res if r is not None and r[0] == 0]
+        lat = np.array([r[3] for r in ok])
+        qw = np.array([r[2] for r in ok])
+        hits_done = sum(n for pl in plans for _, n in pl)
+        leg = {"chunks": len(res), "failed": len(res) - len(ok),
+               "hits_per_s": hits_done / wall if wall > 0 else None,
+               "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+               "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+               "queue_p50_ms": float(np.percentile(qw, 50)) if len(qw) else None,
+               "queue_p99_ms": float(np.percentile(qw, 99)) if len(qw) else None,
+               "peak_bytes": st["peak"], "waits": st["waits"], "releases": st["releases"]}
+        if open_loop:
+            leg["offered_hits_per_s"] = rate * len(streams)
+            fr = []
+            for k, sizes in enumerate(first_rep):
+                parts = [first[(k, j)] for j in range(len(sizes)) if (k, j) in first]
+                if len(parts) < len(sizes):
+                    continue
+                idx = np.concatenate([p[0] for p in parts])
+                lab = np.concatenate([p[1] for p in parts])
+                ends = np.cumsum(sizes)
+                chunk_of = np.searchsorted(ends, idx, side="right")
+                lab_chunk = np.searchsorted(ends, lab, side="right")
+                crossing = np.unique(lab[chunk_of != lab_chunk])
+                fr.append(len(crossing) / max(1, len(np.unique(lab))))
+            leg["straddling_cluster_frac"] = float(np.mean(fr)) if fr else None
+        out[name] = leg
     return out
 
 
 def run_large_sensor(args, dev, torch):
-    """Timepix4-size sensor (448x512, the 2.5 Ghits/s config-1 mix) at
-    args.large_scale of its 512 Mi hits: variant (a) at dt = 128 and 384
-    ticks, variants (c) and (b) at dt = 128; one flush per step, inputs
-    resident on the device, CUDA events on the context stream."""
+    """The Timepix4-size workload: a 448x512 sensor, 512 Mi hits (8 GiB of
+    records) at 2.5 Ghits/s density with the config-1 blob/track mix and ToT
+    up to 1023, drawn as 16 consecutive sub-streams in parallel host threads;
+    every variant of the paper (Section 2, (iii)(a)-(c)): (a) at dt = 128 and
+    384 ticks, (c) and (b) at dt = 128.  One flush per step, inputs resident
+    on the device, CUDA events on the context stream.  Each variant carries
+    its path roofline (hits/s x B_alg against the measured HBM copy rate)
+    and the oracle timed on the host cores on the first --large-oracle-sample
+    hits of the same stream."""
     import synth
+    import oracle
     from paper_2412_11809_gb300 import Clusterer
-    hits, _ = synth.cfg4(scale=args.large_scale, seed=4000)
+    t0 = time.perf_counter()
+    hits, _ = synth.cfg4(scale=args.large_scale, seed=4000, blocks=16)
+    gen_s = time.perf_counter() - t0
     n = len(hits)
     d = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).to(dev)
     stream = torch.cuda.Stream(device=dev)
-    out = {"sensor": "448x512", "hits": n}
+    peak, peak_src = measured_peak_gbs()
+    n_or = min(n, args.large_oracle_sample)
+    sample = np.ascontiguousarray(hits[:n_or])
+    out = {"sensor": "448x512", "hits": n, "scale": args.large_scale,
+           "workload": "448x512 Timepix4-size sensor, 512 Mi hits at 2.5 Ghits/s density, 80% blobs / "
+                       "20% tracks, dead-time refires, ToT <= 1023, window-shuffled (1000 hits)",
+           "generation_s": gen_s, "l2": "inputs larger than L2 (8 GiB per step)"}
     for name, variant, dt, steps in (("local_dt128", "local", 128, 5), ("local_dt384", "local", 384, 5),
                                      ("static_dt128", "static", 128, 3), ("global_dt128", "global", 128, 2)):
         c = Clusterer(448, 512, dt, variant=variant, stream=stream)
         c.push(d)
         c.flush()
         c.sync()
+        _, n_clusters, _ = c.counts()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
@@ -442,8 +510,23 @@ def run_large_sensor(args, dev, torch):
         e1.record(stream)
         e1.synchronize()
         c.sync()
-        out[name] = n * steps / (e0.elapsed_time(e1) / 1e3)
+        ms = e0.elapsed_time(e1) / steps
         c.close()
+        rate = n / (ms / 1e3)
+        b_alg = path_bytes_per_hit(n, n_clusters)
+        t1 = time.perf_counter()
+        lab = oracle.labels(sample, 448, 512, dt, variant)
+        oracle.features(sample, lab)
+        or_s = time.perf_counter() - t1
+        out[name] = {
+            "hits_per_s": rate, "ms_per_step": ms, "steps": steps, "clusters": n_clusters,
+            "roofline": {"bound": "hbm", "achieved": rate * b_alg / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": rate * b_alg / 1e9 / peak, "bytes_per_hit": b_alg,
+                         "peak_source": peak_src},
+            "cpu_baseline": {"value": n_or / or_s, "unit": "hits/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n_or} hits of the same stream, labels + features, "
+                                       f"single thread"}}
+    del d
     return out
 
 
@@ -762,9 +845,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, serving, large-sensor and ingest lines")
     ap.add_argument("--serving-hits", type=int, default=4 * 2**20, help="base hits per serving stream")
     ap.add_argument("--serving-chunks", type=int, default=1024)
+    ap.add_argument("--serving-budget", type=int, default=3 << 30,
+                    help="device-memory budget of the serving loop, bytes")
     ap.add_argument("--batch-scale", type=float, default=1.0)
-    ap.add_argument("--large-scale", type=float, default=0.125,
+    ap.add_argument("--large-scale", type=float, default=1.0,
                     help="fraction of the 512 Mi-hit 448x512 stream for the large-sensor lines")
+    ap.add_argument("--large-oracle-sample", type=int, default=2**20,
+                    help="hits of the 448x512 stream the oracle is timed on, per variant")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -338,6 +338,80 @@ int tpc_cluster_static(const tpc_hit *hits, size_t n, uint32_t width, uint32_t h
                        uint64_t dt, uint64_t *labels, tpc_cluster *records, size_t record_cap,
                        uint64_t *counts, void *stream);
 
+/* Serving loop: detector streams clustered on one GPU under one device-memory
+   budget.  The paper keeps every buffer "in use until retrieved" and hands a
+   thread the next buffer only when one is free (Algorithm 2; Algorithm 3
+   steps 1 and 9, Section 4.1); here a submitted chunk waits in one queue, in
+   submission order, until its stream is idle and the device memory the
+   stream will hold while the chunk runs fits in the budget next to what the
+   other streams hold.  Admitted chunks run at once on their stream's own CUDA
+   stream (chunks of different streams overlap on the GPU), each through a
+   streaming TPC_LOCAL context (open clusters carried on the device,
+   finalised by the ToA watermark, as TPC_OPT_MAX_DISORDER), and their
+   results are copied into the caller's host buffers.  When the chunk at the
+   head of the queue does not fit, the work arrays of idle streams are freed
+   (stream-ordered, without synchronising the device) before it waits;
+   later chunks do not overtake it.  Each stream has a host worker thread. */
+typedef struct tpc_server tpc_server;
+
+typedef struct tpc_server_result {
+    uint64_t tag;        /* the tag the chunk was submitted with */
+    int32_t stream;      /* its stream */
+    int32_t status;      /* TPC_OK, or the chunk's error (TPC_ERR_BUSY: it can
+                            never fit in the budget; TPC_ERR_CAP: cap too small,
+                            n_hits / n_clusters give the sizes needed and the
+                            results are lost; a device error of the step) */
+    uint64_t n_hits;     /* hits finalised by the chunk: labels[k] is the label
+                            of global hit indices[k], k < n_hits, increasing */
+    uint64_t n_clusters; /* cluster records finalised, records[0..n_clusters) */
+    double queue_ms;     /* submission to admission */
+    double latency_ms;   /* submission to results in the caller's buffers */
+} tpc_server_result;
+
+typedef struct tpc_server_stats {
+    uint64_t budget;     /* bytes */
+    uint64_t in_use;     /* bytes held by idle streams plus reserved by running chunks */
+    uint64_t peak;       /* largest in_use so far */
+    uint64_t streams, submitted, admitted, completed, failed, rejected;
+    uint64_t queued;     /* chunks waiting now */
+    uint64_t in_flight;  /* chunks running now */
+    uint64_t waits;      /* chunks that waited at the head of the queue for memory */
+    uint64_t releases;   /* idle streams whose work arrays were freed to make room */
+} tpc_server_stats;
+
+/* A server for the current CUDA device with a budget in bytes (> 0). */
+int tpc_server_create(uint64_t mem_budget, tpc_server **out);
+
+/* Add a detector stream: sensor, time window and the stream's disorder
+   bound t (Section 3.1; 0 < max_disorder < UINT64_MAX).  *id receives its
+   number (0, 1, ...). */
+int tpc_server_add_stream(tpc_server *s, uint32_t width, uint32_t height, uint64_t dt,
+                          uint64_t max_disorder, int *id);
+
+/* Queue a chunk of n host hits of stream id (copied to the device when it is
+   admitted), or, with end_of_stream != 0 and n == 0, the end of the stream
+   (closes every open cluster; no chunk may follow).  The caller keeps
+   `hits` unchanged and the host buffers labels, indices (may be NULL) and
+   records (cap entries each) alive until tpc_server_wait() returns this
+   chunk's result; cap must cover the hits the chunk finalises (at most its
+   own hits plus the stream's open hits).  Chunks of one stream run in
+   submission order.  Never blocks on the device. */
+int tpc_server_submit(tpc_server *s, int id, const tpc_hit *hits, size_t n, uint64_t *labels,
+                      uint64_t *indices, tpc_cluster *records, size_t cap, uint64_t tag,
+                      int end_of_stream);
+
+/* Wait up to timeout_us microseconds (< 0: no limit) for the next completed
+   chunk, in completion order.  TPC_ERR_TIMEOUT if none completed in time;
+   TPC_ERR_STATE if nothing is queued, running or waiting to be returned. */
+int tpc_server_wait(tpc_server *s, tpc_server_result *res, int64_t timeout_us);
+
+/* Counters and memory figures of the server. */
+int tpc_server_stats_get(tpc_server *s, tpc_server_stats *out);
+
+/* Drop queued chunks, let running ones finish, end the worker threads and
+   destroy the streams' contexts. */
+void tpc_server_destroy(tpc_server *s);
+
 const char *tpc_strerror(int status);
 void tpc_destroy(tpc_ctx *ctx);
 

@@ -1,11 +1,12 @@
 """GB300 (sm_103a) clustering of Timepix hits into connected components.
 
 The compute lives in the CUDA library ``_build/libtpc.so`` (C ABI in
-``include/tpc.h``); this package is its binding.  See ``Clusterer`` and, for
-the host-side hit buffer filling of Algorithm 2, ``Filler``.
+``include/tpc.h``); this package is its binding.  See ``Clusterer``, the
+serving loop ``Server`` and, for the host-side hit buffer filling of
+Algorithm 2, ``Filler``.
 """
-from .binding import (CLUSTER_DTYPE, HIT_DTYPE, Clusterer, Filler, TpcError, batch_flush,
+from .binding import (CLUSTER_DTYPE, HIT_DTYPE, Clusterer, Filler, Server, TpcError, batch_flush,
                       load_library)
 
-__all__ = ["CLUSTER_DTYPE", "HIT_DTYPE", "Clusterer", "Filler", "TpcError", "batch_flush",
+__all__ = ["CLUSTER_DTYPE", "HIT_DTYPE", "Clusterer", "Filler", "Server", "TpcError", "batch_flush",
            "load_library"]

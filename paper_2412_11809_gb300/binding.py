@@ -60,6 +60,12 @@ SIGNATURES = {
     "tpc_filler_take": ([_VP, _VP, _VP, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_U64)], _INT),
     "tpc_filler_send": ([_VP, _VP, _VP, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_U64)], _INT),
     "tpc_filler_destroy": ([_VP], None),
+    "tpc_server_create": ([_U64, ctypes.POINTER(_VP)], _INT),
+    "tpc_server_add_stream": ([_VP, _U32, _U32, _U64, _U64, ctypes.POINTER(_INT)], _INT),
+    "tpc_server_submit": ([_VP, _INT, _VP, _SZ, _VP, _VP, _VP, _SZ, _U64, _INT], _INT),
+    "tpc_server_wait": ([_VP, _VP, ctypes.c_int64], _INT),
+    "tpc_server_stats_get": ([_VP, _VP], _INT),
+    "tpc_server_destroy": ([_VP], None),
     "tpc_strerror": ([_INT], ctypes.c_char_p),
     "tpc_destroy": ([_VP], None),
 }
@@ -385,6 +391,106 @@ class Filler:
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.tpc_filler_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class ServerResult(ctypes.Structure):
+    """``tpc_server_result``."""
+    _fields_ = [("tag", ctypes.c_uint64), ("stream", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("n_hits", ctypes.c_uint64), ("n_clusters", ctypes.c_uint64),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    """``tpc_server_stats``."""
+    _fields_ = [(name, ctypes.c_uint64) for name in
+                ("budget", "in_use", "peak", "streams", "submitted", "admitted", "completed",
+                 "failed", "rejected", "queued", "in_flight", "waits", "releases")]
+
+
+class Server:
+    """Serving loop (``tpc_server_*``): detector streams under one device-memory
+    budget; chunks queue until memory and their stream are free.  Host
+    buffers only: ``submit`` takes raw pointers (keep the memory alive until
+    ``wait`` returns the chunk's result) or numpy arrays (kept alive here)."""
+
+    def __init__(self, mem_budget: int):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.tpc_server_create(mem_budget, ctypes.byref(h)), "tpc_server_create")
+        self._h, self._lib = h, lib
+        self._keep = {}
+
+    def add_stream(self, width: int, height: int, dt: int, max_disorder: int) -> int:
+        k = ctypes.c_int()
+        _check(self._lib.tpc_server_add_stream(self._h, width, height, dt, max_disorder,
+                                               ctypes.byref(k)), "tpc_server_add_stream")
+        return k.value
+
+    def submit_ptr(self, stream: int, hits_ptr, n: int, labels_ptr: int, indices_ptr, records_ptr: int,
+                   cap: int, tag: int, end: bool = False):
+        _check(self._lib.tpc_server_submit(self._h, stream, hits_ptr, n, labels_ptr, indices_ptr,
+                                           records_ptr, cap, tag, int(end)), "tpc_server_submit")
+
+    def submit(self, stream: int, hits, tag: int, cap: int | None = None, end: bool = False):
+        """Queue numpy hits (or the end of the stream with hits=None); the
+        result arrays are returned by ``wait`` as (result, labels, indices, records)."""
+        a = None if hits is None else np.ascontiguousarray(hits)
+        if a is not None and a.dtype != HIT_DTYPE:
+            raise TypeError(f"hits must have dtype {HIT_DTYPE}")
+        n = 0 if a is None else len(a)
+        cap = cap if cap is not None else n + (1 << 20)
+        lab = np.empty(cap, dtype=np.uint64)
+        idx = np.empty(cap, dtype=np.uint64)
+        rec = np.empty(cap, dtype=CLUSTER_DTYPE)
+        self._keep[tag] = (a, lab, idx, rec)
+        try:
+            self.submit_ptr(stream, a.ctypes.data if n else None, n, lab.ctypes.data, idx.ctypes.data,
+                            rec.ctypes.data, cap, tag, end)
+        except Exception:
+            self._keep.pop(tag, None)
+            raise
+
+    def wait_raw(self, timeout_s: float | None = None) -> ServerResult | None:
+        """The next completed chunk's result record, or None on timeout."""
+        r = ServerResult()
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        rc = self._lib.tpc_server_wait(self._h, ctypes.byref(r), us)
+        if rc == -5:   # TPC_ERR_TIMEOUT
+            return None
+        _check(rc, "tpc_server_wait")
+        return r
+
+    def wait(self, timeout_s: float | None = None):
+        """(result, labels, indices, records) of the next completed chunk
+        submitted with ``submit``, or None on timeout."""
+        r = self.wait_raw(timeout_s)
+        if r is None:
+            return None
+        _, lab, idx, rec = self._keep.pop(r.tag)
+        return r, lab[:r.n_hits], idx[:r.n_hits], rec[:r.n_clusters]
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.tpc_server_stats_get(self._h, ctypes.byref(st)), "tpc_server_stats_get")
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tpc_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -33,7 +33,8 @@ def _sources() -> list[str]:
 
 def _digest() -> str:
     h = hashlib.sha256()
-    for f in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "tpc.h")]:
+    for f in (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) +
+              sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(INCLUDE, "tpc.h")]):
         h.update(f.encode())
         h.update(open(f, "rb").read())
     h.update(" ".join(ARCH + FLAGS).encode())

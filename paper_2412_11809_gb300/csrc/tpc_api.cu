@@ -20,6 +20,7 @@
 #include <new>
 #include <vector>
 
+#include "ctx_internal.h"
 #include "tpc_internal.cuh"
 
 using namespace tpc;
@@ -42,16 +43,53 @@ std::mutex occ_mu;
 std::vector<OccEntry> occ_cache;
 
 
+// Device memory of every context comes from one stream-ordered pool per
+// device (cudaMallocFromPoolAsync / cudaFreeAsync on the context's stream).
+// Growing or dropping one context's arrays is ordered after that context's
+// own queued work and never synchronises the device, so contexts serving
+// other streams keep running.  The pool keeps up to POOL_KEEP bytes of freed
+// memory for reuse instead of returning it to the driver.
+constexpr int MAX_DEVICES = 64;
+constexpr uint64_t POOL_KEEP = 8ull << 30;
+std::mutex pool_mu;
+cudaMemPool_t pools[MAX_DEVICES] = {};
+
+cudaMemPool_t device_pool(int dev) {
+    if (dev < 0 || dev >= MAX_DEVICES) return nullptr;
+    std::lock_guard<std::mutex> lk(pool_mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = POOL_KEEP;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 // Every allocation of a context goes through these two.  `fault` is the
 // context's TPC_OPT_FAIL_ALLOC countdown (a test hook): while positive it
 // counts the allocations still to succeed, and the one that brings it to
 // zero fails as an out-of-memory would, without calling CUDA.
 bool injected_failure(int64_t *fault) { return fault && *fault > 0 && --*fault == 0; }
 
-cudaError_t dev_alloc(int64_t *fault, void **p, size_t bytes) {
+// Device memory, usable by work queued on `st` after this call (and by other
+// streams once they wait for `st`).
+cudaError_t dev_alloc(int64_t *fault, void **p, size_t bytes, cudaStream_t st, int dev) {
     *p = nullptr;
     if (injected_failure(fault)) return cudaErrorMemoryAllocation;
-    return cudaMalloc(p, bytes);
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+// Free after the work already queued on `st` (which must include every use).
+void dev_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
 }
 
 cudaError_t host_alloc(int64_t *fault, void **p, size_t bytes) {
@@ -64,20 +102,22 @@ struct DevMem {
     std::vector<void *> ptrs;
     size_t bytes = 0;
     int64_t *fault = nullptr;
+    cudaStream_t stream = nullptr;   // the owning context's stream
+    int dev = 0;
     template <class T>
     T *alloc(size_t count, cudaError_t &err) {
         void *p = nullptr;
         if (err != cudaSuccess) return nullptr;
         size_t b = std::max<size_t>(count, 1) * sizeof(T);
         b = (b + 255) & ~size_t(255);
-        err = dev_alloc(fault, &p, b);
+        err = dev_alloc(fault, &p, b, stream, dev);
         if (err != cudaSuccess) return nullptr;
         ptrs.push_back(p);
         bytes += b;
         return static_cast<T *>(p);
     }
     void release() {
-        for (void *p : ptrs) cudaFree(p);
+        for (void *p : ptrs) dev_free(p, stream);
         ptrs.clear();
         bytes = 0;
     }
@@ -90,22 +130,27 @@ struct Workspace {
     Work w{};
     DevMem mem;
 
-    static size_t bytes_for(size_t pos_cap) {
-        const size_t tiles = pos_cap / TILE + MAX_SEGS;
-        // keys, vals (2 each), spix, parent, root_of: 4 B; stot: 2 B; slot; lab_tmp: 8 B
-        return pos_cap * (7 * 4 + 2 + sizeof(Slot) + 8) + pos_cap / 4 +
-               tiles * (4 + 4 + 4 * 4 + RADIX * 4) + MAX_SEGS * (RADIX * 4 + sizeof(Seg)) + (1 << 16);
+    // Bytes ensure(positions) allocates (the same arrays, each rounded up to
+    // 256 bytes as DevMem does).
+    static size_t bytes_for(size_t positions) {
+        const size_t need = std::max<size_t>(((positions + TILE - 1) / TILE) * TILE, TILE);
+        const size_t P = need + TILE, T = need / TILE + MAX_SEGS;
+        auto r = [](size_t count, size_t size) { return ((std::max<size_t>(count, 1) * size) + 255) & ~size_t(255); };
+        return r(MAX_SEGS, sizeof(Seg)) + r(1, sizeof(Prob)) + 3 * r(T, 4) + 5 * r(P, 4) + r(P, 2) +
+               2 * r(P, 4) + r(P, sizeof(Slot)) + r(P, 8) + 2 * r(P / 32 + 1, 4) + 2 * r(2 * T, 4) +
+               r((size_t)RADIX * T, 4) + r((size_t)MAX_SEGS * RADIX, 4);
     }
 
     cudaError_t ensure(size_t positions) {
         size_t need = ((positions + TILE - 1) / TILE) * TILE;
         if (need <= pos_cap && w.seg) return cudaSuccess;
-        cudaDeviceSynchronize();   // in-flight steps may still use the old arrays
-        mem.release();
+        mem.release();   // freed after the steps already queued on the owner's stream
         need = std::max<size_t>(need, TILE);
         pos_cap = need;
         tile_cap = need / TILE + MAX_SEGS;   // segments pad to whole tiles
-        const size_t P = pos_cap + (size_t)MAX_SEGS * TILE, T = tile_cap;
+        // segments are laid out on whole tiles, so `need` (a sum of whole
+        // tiles) covers every position a step uses; one spare tile
+        const size_t P = pos_cap + TILE, T = tile_cap;
         pos_cap = P;
         cudaError_t e = cudaSuccess;
         w.seg = mem.alloc<Seg>(MAX_SEGS, e);
@@ -133,7 +178,8 @@ struct Workspace {
             Prob p{};
             p.tile_cap = (uint32_t)T;
             p.pos_cap = (uint32_t)P;
-            e = cudaMemcpy(w.prob, &p, sizeof(Prob), cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(w.prob, &p, sizeof(Prob), cudaMemcpyHostToDevice, mem.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(mem.stream);   // &p is on this stack
         }
         if (e != cudaSuccess) {
             mem.release();
@@ -152,7 +198,6 @@ struct VarSpace {
     size_t pos_cap = 0, pixels = 0;
     cudaError_t ensure(size_t positions, size_t npixels) {
         if (v.k[0] && positions <= pos_cap && npixels <= pixels) return cudaSuccess;
-        cudaDeviceSynchronize();
         mem.release();
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < 2; ++i) {
@@ -271,6 +316,14 @@ struct tpc_ctx {
     }
 };
 
+// Point the context's device-memory holders at its current stream.
+static void bind_mem(tpc_ctx *c) {
+    for (DevMem *m : {&c->ws.mem, &c->vs.mem, &c->outmem}) {
+        m->stream = c->stream;
+        m->dev = c->device;
+    }
+}
+
 int tpc::occupancy(const void *kernel, int threads, size_t smem) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -293,7 +346,6 @@ int grid_of(const tpc_ctx *c) {
 
 cudaError_t ensure_out(tpc_ctx *c, size_t n) {
     if (n <= c->out_cap && c->d_labels) return cudaSuccess;
-    cudaStreamSynchronize(c->stream);
     c->outmem.release();
     cudaError_t e = cudaSuccess;
     size_t cap = std::max<size_t>(n, 1024);
@@ -420,17 +472,15 @@ int materialise(tpc_ctx *c, size_t more) {
         size_t cap = std::max(need, c->in_cap * 2);
         if (over_budget(c, (cap - c->in_cap) * sizeof(tpc_hit))) return TPC_ERR_BUSY;
         tpc_hit *nb = nullptr;
-        if (dev_alloc(&c->fail_alloc, (void **)&nb, cap * sizeof(tpc_hit)) != cudaSuccess) return TPC_ERR_NOMEM;
+        if (dev_alloc(&c->fail_alloc, (void **)&nb, cap * sizeof(tpc_hit), c->stream, c->device) != cudaSuccess)
+            return TPC_ERR_NOMEM;
         const tpc_hit *src = c->zc ? c->zc : c->in;
         if (c->pending &&
             cudaMemcpyAsync(nb, src, c->pending * sizeof(tpc_hit), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
-            cudaFree(nb);
+            dev_free(nb, c->stream);
             return TPC_ERR_CUDA;
         }
-        if (c->in) {
-            cudaStreamSynchronize(c->stream);
-            cudaFree(c->in);
-        }
+        dev_free(c->in, c->stream);   // after the copy out of it
         c->in = nb;
         c->in_cap = cap;
     } else if (c->zc) {
@@ -458,9 +508,11 @@ int ensure_stream_buffers(tpc_ctx *c, size_t chunk) {
     tpc_hit *nb[2] = {nullptr, nullptr};
     uint64_t *ng[2] = {nullptr, nullptr};
     for (int i = 0; i < 2; ++i) {
-        if (dev_alloc(&c->fail_alloc, (void **)&nb[i], (ncarry + nchunk) * sizeof(tpc_hit)) != cudaSuccess ||
-            dev_alloc(&c->fail_alloc, (void **)&ng[i], (ncarry + nchunk) * sizeof(uint64_t)) != cudaSuccess) {
-            for (int j = 0; j < 2; ++j) { cudaFree(nb[j]); cudaFree(ng[j]); }
+        if (dev_alloc(&c->fail_alloc, (void **)&nb[i], (ncarry + nchunk) * sizeof(tpc_hit), c->stream, c->device) !=
+                cudaSuccess ||
+            dev_alloc(&c->fail_alloc, (void **)&ng[i], (ncarry + nchunk) * sizeof(uint64_t), c->stream, c->device) !=
+                cudaSuccess) {
+            for (int j = 0; j < 2; ++j) { dev_free(nb[j], c->stream); dev_free(ng[j], c->stream); }
             return TPC_ERR_NOMEM;
         }
     }
@@ -473,10 +525,9 @@ int ensure_stream_buffers(tpc_ctx *c, size_t chunk) {
         cudaMemcpyAsync(ng[next] + (ncarry - nc), c->sgidx[next] + (c->carry_cap - nc), nc * sizeof(uint64_t),
                         cudaMemcpyDeviceToDevice, c->stream);
     }
-    cudaStreamSynchronize(c->stream);
-    for (int i = 0; i < 2; ++i) {
-        cudaFree(c->sbuf[i]);
-        cudaFree(c->sgidx[i]);
+    for (int i = 0; i < 2; ++i) {   // freed after the copies above, in stream order
+        dev_free(c->sbuf[i], c->stream);
+        dev_free(c->sgidx[i], c->stream);
         c->sbuf[i] = nb[i];
         c->sgidx[i] = ng[i];
     }
@@ -492,7 +543,7 @@ int stream_step(tpc_ctx *c, size_t n, bool close_all) {
     const size_t positions = c->carry_ub + n;
     c->has_result = false;   // the workspace may move: the last result is gone
     if (c->ws.ensure(positions) != cudaSuccess) return TPC_ERR_NOMEM;
-    if (ensure_out(c, c->carry_cap + c->chunk_cap) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (ensure_out(c, positions) != cudaSuccess) return TPC_ERR_NOMEM;   // >= hits this step can finalise
     Seg s = base_seg(c);
     s.carry_in = c->sbuf[in];
     s.carry_gidx_in = c->sgidx[in];
@@ -560,6 +611,8 @@ int tpc_create(uint32_t width, uint32_t height, uint64_t dt, int variant, tpc_ct
     if (init_kernel_attributes() != cudaSuccess) { delete c; return TPC_ERR_CUDA; }
     bool ok = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess;
     c->own_stream = ok;
+    bind_mem(c);
+    ok = ok && device_pool(c->device) != nullptr;
     ok = ok && cudaMallocHost(&c->h_seg, sizeof(Seg) * MAX_SEGS * SEG_RING) == cudaSuccess;
     for (int i = 0; ok && i < SEG_RING; ++i)
         ok = cudaEventCreateWithFlags(&c->seg_ev[i], cudaEventDisableTiming) == cudaSuccess;
@@ -582,9 +635,10 @@ int tpc_set_option(tpc_ctx *c, int key, uint64_t value) {
         if (value == 0) return TPC_ERR_ARG;
         if (value != ~0ull && !c->ss) {   // the stream state first: the option stands only with it
             StreamState *ss = nullptr;
-            if (dev_alloc(&c->fail_alloc, (void **)&ss, sizeof(StreamState)) != cudaSuccess) return TPC_ERR_NOMEM;
+            if (dev_alloc(&c->fail_alloc, (void **)&ss, sizeof(StreamState), c->stream, c->device) != cudaSuccess)
+                return TPC_ERR_NOMEM;
             if (cudaMemsetAsync(ss, 0, sizeof(StreamState), c->stream) != cudaSuccess) {
-                cudaFree(ss);
+                dev_free(ss, c->stream);
                 return TPC_ERR_CUDA;
             }
             c->ss = ss;
@@ -606,6 +660,7 @@ int tpc_set_option(tpc_ctx *c, int key, uint64_t value) {
             if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return TPC_ERR_CUDA;
             c->own_stream = true;
         }
+        bind_mem(c);   // the old stream is idle: later frees may go on the new one
         return TPC_OK;
     }
     case TPC_OPT_CTAS_PER_SM:
@@ -871,7 +926,11 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
     for (int i = 0; i < n; ++i) ctxs[i]->has_result = false;   // workspaces may move
     size_t positions = 0;
     for (int i = 0; i < n; ++i) positions += ((ctxs[i]->pending + TILE - 1) / TILE) * TILE;
-    // every context's pending copies must land before the lead stream reads them
+    // output buffers first (allocated on each context's own stream), then
+    // every context's pending copies and allocations must land before the
+    // lead stream uses them
+    for (int i = 0; i < n; ++i)
+        if (ensure_out(ctxs[i], ctxs[i]->pending) != cudaSuccess) return TPC_ERR_NOMEM;
     for (int i = 1; i < n; ++i) {
         if (cudaEventRecord(ctxs[i]->done_ev, ctxs[i]->stream) != cudaSuccess ||
             cudaStreamWaitEvent(lead->stream, ctxs[i]->done_ev, 0) != cudaSuccess)
@@ -881,7 +940,6 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
     std::vector<Seg> segs(n);
     for (int i = 0; i < n; ++i) {
         tpc_ctx *c = ctxs[i];
-        if (ensure_out(c, c->pending) != cudaSuccess) return TPC_ERR_NOMEM;
         Seg s = base_seg(c);
         s.hits = c->zc ? c->zc : c->in;
         s.out_labels = c->d_labels;
@@ -942,6 +1000,66 @@ int tpc_forest(tpc_ctx *c, uint32_t *parent, uint32_t *input_pos, size_t cap, si
     }
     return TPC_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal interface of the serving loop (server.cu).
+
+size_t tpc::ctx_projected_bytes(tpc_ctx *c, size_t n) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    // the growth rules of ensure_stream_buffers, stream_step and ensure_out,
+    // with the carry at its upper bound (the device holds the exact count)
+    size_t carry_cap = c->carry_cap, chunk_cap = c->chunk_cap;
+    if (n > chunk_cap || c->carry_ub + n > carry_cap || !c->sbuf[0]) {
+        carry_cap = std::max<size_t>({carry_cap, 2 * (c->carry_ub + n), 1 << 16});
+        chunk_cap = std::max<size_t>({chunk_cap, n, 1 << 16});
+    }
+    const size_t stream_bytes = 2 * (carry_cap + chunk_cap) * (sizeof(tpc_hit) + sizeof(uint64_t));
+    const size_t positions = c->carry_ub + n;
+    const size_t ws = positions <= c->ws.pos_cap && c->ws.w.seg ? c->ws.mem.bytes : Workspace::bytes_for(positions);
+    const size_t out_n = std::max<size_t>(positions, 1024);
+    const size_t out = out_n <= c->out_cap && c->d_labels ? c->outmem.bytes
+                                                          : 2 * ((out_n * 8 + 255) & ~size_t(255)) +
+                                                                ((out_n * sizeof(tpc_cluster) + 255) & ~size_t(255));
+    return ws + out + stream_bytes + c->in_cap * sizeof(tpc_hit);
+}
+
+size_t tpc::ctx_held_bytes(tpc_ctx *c) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    return c->device_bytes();
+}
+
+void tpc::ctx_release_scratch(tpc_ctx *c) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->ws.mem.release();   // stream-ordered: after the context's queued work
+    c->ws.w = Work{};
+    c->ws.pos_cap = c->ws.tile_cap = 0;
+    ++c->ws.gen;
+    c->outmem.release();
+    c->d_labels = c->d_index = nullptr;
+    c->d_rec = nullptr;
+    c->out_cap = 0;
+    c->vs.mem.release();
+    c->vs.v = VarWork{};
+    c->vs.pos_cap = c->vs.pixels = 0;
+    c->has_result = false;
+}
+
+int tpc::ctx_settle(tpc_ctx *c) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->ss || !c->carry_ub) return TPC_OK;
+    uint32_t nc = 0;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+        cudaMemcpy(&nc, &c->ss->n_carry, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TPC_ERR_CUDA;
+    c->carry_ub = nc;   // the exact count: the next push's sizes follow it
+    return TPC_OK;
+}
+
+cudaStream_t tpc::ctx_stream(tpc_ctx *c) { return c->stream; }
+
+extern "C" {
 
 int tpc_device_bytes(tpc_ctx *c, size_t *bytes) {
     if (!c || !bytes) return TPC_ERR_ARG;
@@ -1017,7 +1135,8 @@ int tpc_restore(tpc_ctx *c, const void *buf, size_t n) {
         c->carry_ub = 0;
     }
     if (!c->ss) {
-        if (dev_alloc(&c->fail_alloc, (void **)&c->ss, sizeof(StreamState)) != cudaSuccess) return TPC_ERR_NOMEM;
+        if (dev_alloc(&c->fail_alloc, (void **)&c->ss, sizeof(StreamState), c->stream, c->device) != cudaSuccess)
+            return TPC_ERR_NOMEM;
         if (cudaMemsetAsync(c->ss, 0, sizeof(StreamState), c->stream) != cudaSuccess) return TPC_ERR_CUDA;
         c->scur = 1;
         c->carry_ub = 0;
@@ -1074,16 +1193,16 @@ const char *tpc_strerror(int status) {
 
 void tpc_destroy(tpc_ctx *c) {
     if (!c) return;
-    if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    c->ws.mem.release();
+    c->ws.mem.release();   // stream-ordered frees, after the context's queued work
     c->outmem.release();
-    cudaFree(c->in);
-    for (int i = 0; i < 2; ++i) { cudaFree(c->sbuf[i]); cudaFree(c->sgidx[i]); }
-    cudaFree(c->ss);
+    c->vs.mem.release();
+    dev_free(c->in, c->stream);
+    for (int i = 0; i < 2; ++i) { dev_free(c->sbuf[i], c->stream); dev_free(c->sgidx[i], c->stream); }
+    dev_free(c->ss, c->stream);
+    if (c->stream) cudaStreamSynchronize(c->stream);
     cudaFree(c->own_res_seg);
     cudaFree(c->own_res_prob);
-    c->vs.mem.release();
     if (c->h_flag) cudaFreeHost(c->h_flag);
     if (c->h_seg) cudaFreeHost(c->h_seg);
     if (c->h_stage) cudaFreeHost(c->h_stage);

@@ -65,8 +65,8 @@ def sampled_cluster_check(hits, labels, width, height, dt, n_samples, rng):
         lo = int(hits["toa"][members].min())
         hi = int(hits["toa"][members].max())
         while True:
-            a = np.searchsorted(toa_sorted, max(lo - 2 * dt, 0), side="left")
-            b = np.searchsorted(toa_sorted, hi + 2 * dt, side="right")
+            a = np.searchsorted(toa_sorted, np.uint64(max(lo - 2 * dt, 0)), side="left")
+            b = np.searchsorted(toa_sorted, np.uint64(hi + 2 * dt), side="right")
             idx = np.sort(order[a:b])
             sub = hits[idx]
             sl = oracle.labels(sub, width, height, dt)

@@ -1,0 +1,134 @@
+"""Parity at the full size of the Timepix4 workload: a 448x512 sensor, 512 Mi
+hits at 2.5 Ghits/s density, the blob/track mix with ToT up to 1023, every
+variant the paper defines (Section 2, (iii)(a)-(c)).
+
+* (b) and (c) at dt = 128 ticks: every label and every cluster record against
+  the oracle's sweep over the whole stream (the two oracle runs take a few
+  minutes of host time; they run in threads while the device works, the C
+  oracle releasing the GIL).
+* (a) at dt = 128 and 384 ticks: sampled clusters, each checked exactly.  A
+  component of (a) has sorted ToAs with gaps of at most dt, so the oracle on
+  every hit whose ToA lies within 2 dt of the cluster's span (found by the
+  t-ordering of the stream, Section 3.1, from running extrema) gives the
+  whole component, provided no member of it lies within dt of the window's
+  edge; the window widens until that holds.  The component must equal the
+  GPU cluster as an index set (its size checked against a count of every
+  label), and the cluster's record must equal the oracle's features of it.
+
+The stream is drawn as 16 consecutive sub-streams in parallel host threads
+(``synth.generate_blocked``)."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import assert_features_equal
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2412_11809_gb300 import Clusterer  # noqa: E402
+
+W, H = 448, 512
+N_SAMPLES = 40
+
+
+@pytest.fixture(scope="module")
+def stream():
+    hits, t = synth.cfg4(scale=1.0, seed=4000, blocks=16)
+    assert len(hits) == 512 * 2**20
+    return hits, t
+
+
+def _gpu(d_hits, dt, variant):
+    with Clusterer(W, H, dt, variant) as c:
+        c.push(d_hits)
+        c.flush()
+        lab = c.labels()
+        rec = c.features()
+    return lab, rec
+
+
+class _Window:
+    """Hits with ToA in [a, b], found from running extrema of a t-ordered stream."""
+
+    def __init__(self, hits):
+        self.toa = hits["toa"]
+        self.run_max = np.maximum.accumulate(self.toa)
+        self.suf_min = np.minimum.accumulate(self.toa[::-1])[::-1]
+
+    def __call__(self, a, b):
+        a, b = np.uint64(a), np.uint64(b)   # no promotion of the uint64 arrays to float
+        i = int(np.searchsorted(self.run_max, a, side="left"))   # every hit before i has toa < a
+        j = int(np.searchsorted(self.suf_min, b, side="right"))  # every hit from j on has toa > b
+        idx = np.arange(i, j)
+        return idx[(self.toa[i:j] >= a) & (self.toa[i:j] <= b)]
+
+
+def _check_local_sampled(hits, win, lab, rec, dt, rng):
+    counts = np.bincount(lab.astype(np.int64), minlength=len(hits))
+    rec_labels = np.ascontiguousarray(rec["label"])
+    seen = set()
+    for i in rng.choice(len(hits), size=N_SAMPLES, replace=False):
+        label = int(lab[i])
+        if label in seen:
+            continue
+        seen.add(label)
+        lo = hi = int(hits["toa"][i])
+        while True:
+            idx = win(max(lo - 2 * dt, 0), hi + 2 * dt)
+            sub = hits[idx]
+            sl = oracle.labels(sub, W, H, dt)
+            pos = int(np.searchsorted(idx, i))
+            comp = idx[sl == sl[pos]]
+            clo, chi = int(hits["toa"][comp].min()), int(hits["toa"][comp].max())
+            if clo - dt > lo - 2 * dt and chi + dt < hi + 2 * dt:
+                break
+            lo, hi = min(lo, clo), max(hi, chi)
+        members = idx[lab[idx] == label]
+        np.testing.assert_array_equal(members, comp, err_msg=f"cluster of hit {i}")
+        assert int(counts[label]) == len(comp), f"cluster of hit {i} has members outside its window"
+        assert int(comp.min()) == label
+        want = oracle.features(hits[comp], np.full(len(comp), 0, dtype=np.uint64))
+        want["label"] = label
+        k = int(np.searchsorted(rec_labels, np.uint64(label)))
+        assert_features_equal(rec[k:k + 1], want)
+    return len(seen)
+
+
+def test_fullsize_448x512_all_variants(stream):
+    hits, _ = stream
+    want = {}
+
+    def run_oracle(variant):
+        lab = oracle.labels(hits, W, H, 128, variant)
+        want[variant] = (lab, oracle.features(hits, lab))
+
+    threads = [threading.Thread(target=run_oracle, args=(v,)) for v in ("global", "static")]
+    for th in threads:
+        th.start()
+    try:
+        d_hits = torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).cuda()
+        got = {v: _gpu(d_hits, 128, v) for v in ("global", "static")}
+        win = _Window(hits)
+        rng = np.random.default_rng(4128)
+        for dt in (128, 384):
+            lab, rec = _gpu(d_hits, dt, "local")
+            assert _check_local_sampled(hits, win, lab, rec, dt, rng) >= N_SAMPLES // 2
+            del lab, rec
+        del d_hits
+    finally:
+        for th in threads:
+            th.join()
+    for v in ("global", "static"):
+        lab, rec = got[v]
+        wl, wr = want[v]
+        if not np.array_equal(lab, wl):
+            bad = np.flatnonzero(lab != wl)
+            raise AssertionError(f"({v}) {len(bad)} labels differ; first at {bad[:5]}")
+        assert_features_equal(rec, wr)
