@@ -582,11 +582,14 @@ def run_ingest(hits, t, dev, torch, chunk=2**20):
 
 
 def run_batched(args, dev, torch):
-    """16 detectors (ten 256x256, six 448x512): one batched step (one CUDA-graph
-    replay, persistent CTAs over every detector's tiles) against one flush per
-    detector, inputs resident on the device."""
+    """16 detectors (ten 256x256, six 448x512), chunk sizes log-uniform in
+    10k-8M hits: one batched step (one CUDA-graph replay, persistent CTAs
+    over every detector's tiles) with the default launch choices, then with
+    the choices the autotuner (tpc_tune_batch) picks for this batch, against
+    one flush per detector; inputs resident on the device."""
+    import tempfile
     import synth
-    from paper_2412_11809_gb300 import Clusterer, batch_flush
+    from paper_2412_11809_gb300 import Clusterer, batch_flush, tune_batch
     dets = synth.cfg2(scale=args.batch_scale, seed=2000)
     dev_hits = [torch.from_numpy(h.view(np.uint8).reshape(-1, 16)).to(dev) for _, _, h, _, _ in dets]
     n_total = sum(len(h) for _, _, h, _, _ in dets)
@@ -607,22 +610,37 @@ def run_batched(args, dev, torch):
         for c in ctxs:
             c.sync()
 
-    res = {}
-    for name, fn in (("batched", batched), ("one_launch_per_detector", single)):
+    def timed(fn, reps=5):
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(3):
+        for _ in range(reps):
             fn()
         e1.record(stream)
         e1.synchronize()
-        res[name] = n_total * 3 / (e0.elapsed_time(e1) / 1e3)
+        return n_total * reps / (e0.elapsed_time(e1) / 1e3)
+
+    res = {"untuned": timed(batched), "one_launch_per_detector": timed(single)}
+    cache = os.path.join(tempfile.gettempdir(), "tpc_tune_cache.txt")
+    for c, d in zip(ctxs, dev_hits):
+        c.push(d)
+    t0 = time.perf_counter()
+    rep = tune_batch(ctxs, cache, force=True)
+    tune_s = time.perf_counter() - t0
+    batch_flush(ctxs)            # the tuner leaves the batch pending
+    for c in ctxs:
+        c.sync()
+    res["tuned"] = timed(batched)
     for c in ctxs:
         c.close()
-    return {"detectors": len(dets), "hits": n_total, "hits_per_s": res["batched"],
-            "one_launch_per_detector_hits_per_s": res["one_launch_per_detector"]}
+    return {"detectors": len(dets), "hits": n_total, "hits_per_s": res["tuned"],
+            "untuned_hits_per_s": res["untuned"],
+            "one_launch_per_detector_hits_per_s": res["one_launch_per_detector"],
+            "tuner": {"chosen": rep.chosen.as_dict(), "trials": rep.trials,
+                      "untuned_ms": rep.untuned_ms, "tuned_ms": rep.tuned_ms, "seconds": tune_s,
+                      "key": rep.key.decode()}}
 
 
 def run_gpu(args):

@@ -173,6 +173,61 @@ int tpc_cluster_features(tpc_ctx *ctx, tpc_cluster *out, size_t cap, size_t *n_o
    first context's stream; every context's stream waits for it. */
 int tpc_batch_flush(tpc_ctx **ctxs, int n);
 
+/* Launch choices of a context's processing steps and of the batches it
+   leads (tpc_batch_flush uses the first context's).  Results never depend
+   on them; only the time does.  The paper sizes its GPU work by hand (at
+   least 10,000 hits per thread, Section 4.1); here the work per CTA is a
+   tile of 4096 hits and these choices set how the launches fill the GPU. */
+typedef struct tpc_tuning {
+    uint8_t ctas_sort;    /* CTAs per SM of the tile sort and merge, 0 = as many as fit */
+    uint8_t ctas_link;    /* CTAs per SM of the link kernels, 0 = as many as fit */
+    uint8_t ctas_acc;     /* CTAs per SM of the feature kernel, 0 = as many as fit */
+    uint8_t ctas_out;     /* CTAs per SM of the label and record kernels, 0 = as many as fit */
+    uint16_t acc_span;    /* positions per pass of the feature kernel: 512, 1024 or 2048
+                             (0 = 1024, the default) */
+    uint8_t general_link; /* bit 0: sensors the shared-memory pixel table covers at once,
+                             bit 1: sensors it covers in bands, take the general link kernel */
+    uint8_t order;        /* batches: 0 = contexts in the given order, 1 = most hits first */
+} tpc_tuning;             /* 8 bytes; all zero = the defaults */
+
+/* Set (t, or the defaults if t is NULL) / read a context's launch choices.
+   TPC_ERR_ARG for a value outside the ranges above (CTA counts <= 64). */
+int tpc_set_tuning(tpc_ctx *ctx, const tpc_tuning *t);
+int tpc_get_tuning(tpc_ctx *ctx, tpc_tuning *t);
+
+typedef struct tpc_tune_report {
+    tpc_tuning chosen;    /* the choices now set on ctxs[0] */
+    uint32_t from_cache;  /* 1: taken from the cache file; nothing was timed */
+    uint32_t trials;      /* launch choices timed */
+    double untuned_ms;    /* median device time of the batch with the defaults */
+    double tuned_ms;      /* with the chosen ones (from the cache: as stored) */
+    char key[192];        /* the cache key of this batch */
+} tpc_tune_report;
+
+#define TPC_TUNE_FORCE 1  /* time the candidates even if the cache has the key */
+
+/* Autotuner of the batched step: with the same arguments and preconditions
+   as tpc_batch_flush (every context has pending hits), look the batch's key
+   up in the cache file (GPU name and SM count, each sensor geometry with the
+   bucket floor(log2(hits)) of its pending hits, the number of contexts) or,
+   if absent (or with TPC_TUNE_FORCE), time the pending batch itself, which
+   stays pending: the defaults, then coordinate descent over the fields of
+   tpc_tuning, two passes, three timed runs per candidate, a change kept if
+   its median improves by more than 1 %.  Sets the choice on ctxs[0] and
+   appends it to the cache file (cache_path NULL: no cache).  Work is
+   ordered on ctxs[0]'s stream and waited for. */
+int tpc_tune_batch(tpc_ctx **ctxs, int n, const char *cache_path, int flags, tpc_tune_report *rep);
+
+/* The tuner's cache file, host only (no CUDA call): one line per entry,
+   "key<TAB>ctas_sort ctas_link ctas_acc ctas_out acc_span general_link
+   order<TAB>ms", the last line with a key winning; lines that do not parse
+   are skipped.  lookup: TPC_ERR_STATE if the file or the key is absent;
+   *ms (may be NULL) receives the stored time.  store appends a line;
+   TPC_ERR_ARG for an invalid tuning, an empty key or one holding a tab or
+   newline, or a file that cannot be written. */
+int tpc_tune_cache_lookup(const char *path, const char *key, tpc_tuning *out, double *ms);
+int tpc_tune_cache_store(const char *path, const char *key, const tpc_tuning *t, double ms);
+
 /* Number of hits finalised, clusters finalised and hits carried (open) by
    the last processing step.  Waits for the context's work. */
 int tpc_counts(tpc_ctx *ctx, size_t *n_hits, size_t *n_clusters, size_t *n_open);

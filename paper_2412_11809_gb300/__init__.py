@@ -5,8 +5,8 @@ The compute lives in the CUDA library ``_build/libtpc.so`` (C ABI in
 serving loop ``Server`` and, for the host-side hit buffer filling of
 Algorithm 2, ``Filler``.
 """
-from .binding import (CLUSTER_DTYPE, HIT_DTYPE, Clusterer, Filler, Server, TpcError, batch_flush,
-                      load_library)
+from .binding import (CLUSTER_DTYPE, HIT_DTYPE, Clusterer, Filler, Server, TpcError, Tuning,
+                      batch_flush, load_library, tune_batch)
 
-__all__ = ["CLUSTER_DTYPE", "HIT_DTYPE", "Clusterer", "Filler", "Server", "TpcError", "batch_flush",
-           "load_library"]
+__all__ = ["CLUSTER_DTYPE", "HIT_DTYPE", "Clusterer", "Filler", "Server", "TpcError", "Tuning",
+           "batch_flush", "load_library", "tune_batch"]

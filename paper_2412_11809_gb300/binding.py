@@ -66,11 +66,37 @@ SIGNATURES = {
     "tpc_server_wait": ([_VP, _VP, ctypes.c_int64], _INT),
     "tpc_server_stats_get": ([_VP, _VP], _INT),
     "tpc_server_destroy": ([_VP], None),
+    "tpc_set_tuning": ([_VP, _VP], _INT),
+    "tpc_get_tuning": ([_VP, _VP], _INT),
+    "tpc_tune_batch": ([ctypes.POINTER(_VP), _INT, ctypes.c_char_p, _INT, _VP], _INT),
+    "tpc_tune_cache_lookup": ([ctypes.c_char_p, ctypes.c_char_p, _VP, ctypes.POINTER(ctypes.c_double)], _INT),
+    "tpc_tune_cache_store": ([ctypes.c_char_p, ctypes.c_char_p, _VP, ctypes.c_double], _INT),
     "tpc_strerror": ([_INT], ctypes.c_char_p),
     "tpc_destroy": ([_VP], None),
 }
 
 _lib = None
+
+
+class Tuning(ctypes.Structure):
+    """``tpc_tuning``: launch choices (results never depend on them)."""
+    _fields_ = [("ctas_sort", ctypes.c_uint8), ("ctas_link", ctypes.c_uint8),
+                ("ctas_acc", ctypes.c_uint8), ("ctas_out", ctypes.c_uint8),
+                ("acc_span", ctypes.c_uint16), ("general_link", ctypes.c_uint8),
+                ("order", ctypes.c_uint8)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class TuneReport(ctypes.Structure):
+    """``tpc_tune_report``."""
+    _fields_ = [("chosen", Tuning), ("from_cache", ctypes.c_uint32), ("trials", ctypes.c_uint32),
+                ("untuned_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double),
+                ("key", ctypes.c_char * 192)]
+
+
+assert ctypes.sizeof(Tuning) == 8 and ctypes.sizeof(TuneReport) == 224
 
 
 class TpcError(RuntimeError):
@@ -288,6 +314,18 @@ class Clusterer:
                                     ctypes.byref(n)), "tpc_forest")
         return parent, pos
 
+    def set_tuning(self, tuning: "Tuning | dict | None"):
+        """``tpc_set_tuning``: a Tuning, a dict of its fields, or None (defaults)."""
+        if isinstance(tuning, dict):
+            tuning = Tuning(**tuning)
+        _check(self._lib.tpc_set_tuning(self._h, None if tuning is None else ctypes.byref(tuning)),
+               "tpc_set_tuning")
+
+    def tuning(self) -> Tuning:
+        t = Tuning()
+        _check(self._lib.tpc_get_tuning(self._h, ctypes.byref(t)), "tpc_get_tuning")
+        return t
+
     def device_bytes(self) -> int:
         b = ctypes.c_size_t()
         _check(self._lib.tpc_device_bytes(self._h, ctypes.byref(b)), "tpc_device_bytes")
@@ -317,6 +355,36 @@ def batch_flush(clusterers) -> None:
     lib = load_library()
     arr = (ctypes.c_void_p * len(clusterers))(*[c.handle.value for c in clusterers])
     _check(lib.tpc_batch_flush(arr, len(clusterers)), "tpc_batch_flush")
+
+
+def tune_batch(clusterers, cache_path: str | None = None, force: bool = False) -> TuneReport:
+    """``tpc_tune_batch``: choose (or load from the cache file) the launch
+    choices of the pending batch; they are set on ``clusterers[0]``."""
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(clusterers))(*[c.handle.value for c in clusterers])
+    rep = TuneReport()
+    _check(lib.tpc_tune_batch(arr, len(clusterers), None if cache_path is None else cache_path.encode(),
+                              1 if force else 0, ctypes.byref(rep)), "tpc_tune_batch")
+    return rep
+
+
+def tune_cache_lookup(path: str, key: str):
+    """(Tuning, ms) stored for key in the tuner's cache file, or None."""
+    lib = load_library()
+    t, ms = Tuning(), ctypes.c_double()
+    rc = lib.tpc_tune_cache_lookup(path.encode(), key.encode(), ctypes.byref(t), ctypes.byref(ms))
+    if rc == -10:   # TPC_ERR_STATE: no such file or key
+        return None
+    _check(rc, "tpc_tune_cache_lookup")
+    return t, ms.value
+
+
+def tune_cache_store(path: str, key: str, tuning: "Tuning | dict", ms: float):
+    lib = load_library()
+    if isinstance(tuning, dict):
+        tuning = Tuning(**tuning)
+    _check(lib.tpc_tune_cache_store(path.encode(), key.encode(), ctypes.byref(tuning), ms),
+           "tpc_tune_cache_store")
 
 
 class Filler:

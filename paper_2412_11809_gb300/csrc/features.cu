@@ -19,9 +19,12 @@
 namespace tpc {
 
 constexpr int ACC_THREADS = 512;
-constexpr int ACC_SPAN = 1024;                    // sorted positions per pass (measured best)
-constexpr int ACC_ITEMS = ACC_SPAN / ACC_THREADS;
-constexpr int ACC_SMEM = 2 * ACC_SPAN * (int)sizeof(uint32_t) + 3 * ACC_SPAN * (int)sizeof(unsigned long long);
+// Sorted positions per pass (ACC_SPAN): 1024 by default (measured best on
+// the 256x256 stream); 512 and 2048 are tuning choices.
+template <int ACC_SPAN>
+constexpr int acc_smem() {
+    return 2 * ACC_SPAN * (int)sizeof(uint32_t) + 3 * ACC_SPAN * (int)sizeof(unsigned long long);
+}
 
 // Roots and features in (ToA, position) order, where a cluster's hits sit
 // close together.  Each pass over ACC_SPAN sorted positions finds every
@@ -36,7 +39,9 @@ constexpr int ACC_SMEM = 2 * ACC_SPAN * (int)sizeof(uint32_t) + 3 * ACC_SPAN * (
 // shared-memory counter (size << 32 | sum ToT: a span holds at most ACC_SPAN
 // hits of ToT < 2^16, so neither part overflows), and the last key is kept
 // only when a streaming watermark needs it.
-__global__ void __launch_bounds__(ACC_THREADS, 4) k_accumulate(Work w) {
+template <int ACC_SPAN>
+__global__ void __launch_bounds__(ACC_THREADS, ACC_SPAN >= 2048 ? 2 : 4) k_accumulate(Work w) {
+    constexpr int ACC_ITEMS = ACC_SPAN / ACC_THREADS;
     extern __shared__ __align__(16) unsigned char acc_raw[];
     unsigned long long *a_wx = reinterpret_cast<unsigned long long *>(acc_raw);
     unsigned long long *a_wy = a_wx + ACC_SPAN, *a_st = a_wy + ACC_SPAN;
@@ -376,22 +381,36 @@ __global__ void k_stream_end(Work w) {
 }
 
 cudaError_t init_features_attributes() {
-    return cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, ACC_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_accumulate<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         acc_smem<512>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_accumulate<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, acc_smem<1024>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_accumulate<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, acc_smem<2048>());
+    return e;
+}
+
+template <int SPAN>
+static void launch_accumulate(const Work &w, const Launch &L) {
+    k_accumulate<SPAN><<<L.fit(k_accumulate<SPAN>, ACC_THREADS, acc_smem<SPAN>(), G_ACC), ACC_THREADS,
+                         acc_smem<SPAN>(), L.stream>>>(w);
 }
 
 void launch_features(const Work &w, const Launch &L) {
-    k_accumulate<<<L.fit(k_accumulate, ACC_THREADS, ACC_SMEM), ACC_THREADS, ACC_SMEM, L.stream>>>(w);
+    if (L.tune.acc_span == 512) launch_accumulate<512>(w, L);
+    else if (L.tune.acc_span == 2048) launch_accumulate<2048>(w, L);
+    else launch_accumulate<1024>(w, L);
     L.mark("k_accumulate");
 }
 
 void launch_outputs(const Work &w, const Launch &L) {
-    k_labels<<<L.fit(k_labels, 256, 0), 256, 0, L.stream>>>(w);
+    k_labels<<<L.fit(k_labels, 256, 0, G_OUT), 256, 0, L.stream>>>(w);
     L.mark("k_labels");
     k_tile_scan<<<MAX_SEGS, 1024, 0, L.stream>>>(w);
     L.mark("k_tile_scan");
-    k_records<<<L.fit(k_records, TILE_WORDS, 0), TILE_WORDS, 0, L.stream>>>(w);
+    k_records<<<L.fit(k_records, TILE_WORDS, 0, G_OUT), TILE_WORDS, 0, L.stream>>>(w);
     L.mark("k_records");
-    k_stream_compact<<<L.fit(k_stream_compact, TILE_WORDS, 0), TILE_WORDS, 0, L.stream>>>(w);
+    k_stream_compact<<<L.fit(k_stream_compact, TILE_WORDS, 0, G_OUT), TILE_WORDS, 0, L.stream>>>(w);
     L.mark("k_stream_compact");
     k_stream_end<<<1, 256, 0, L.stream>>>(w);
     L.mark("k_stream_end");

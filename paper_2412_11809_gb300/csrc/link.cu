@@ -51,6 +51,16 @@ __device__ __forceinline__ uint32_t table_rows(uint32_t W, uint32_t H) {
     return (H + rpb - 1) / rpb <= TAB_MAX_BANDS ? rpb : 0;
 }
 __device__ __forceinline__ bool table_mode(uint32_t W, uint32_t H) { return table_rows(W, H) != 0; }
+
+// Host view of the same rule: bands of the table for a W x H sensor (0 =
+// the sensor takes k_tile_link).
+int link_bands(uint32_t W, uint32_t H) {
+    const uint32_t W2 = W + 2;
+    if (W2 * 3 > TAB_CAP) return 0;
+    const uint32_t rpb = TAB_CAP / W2 - 2;
+    const uint32_t nb = (H + rpb - 1) / rpb;
+    return nb <= TAB_MAX_BANDS ? (int)nb : 0;
+}
 constexpr int NBUCKETS = 2048;                // hashed 4x4-pixel cells
 constexpr int HALO_BATCH = 2048;
 constexpr int BORDER_THREADS = 256;
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         const uint32_t n_t = end - begin, W = g.width, H = g.height, dt = g.dt;
-        if (u < n_large && table_mode(W, H)) continue;   // done by k_tile_link_table
+        if (u < n_large && table_mode(W, H) && !g.link_general) continue;   // done by k_tile_link_table
         const uint32_t cw = (W + 3) >> 2;
         {
             constexpr int ITEMS = TILE / LINK_THREADS;
@@ -493,7 +503,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         const uint32_t W = g.width, H = g.height, dt = g.dt;
-        const uint32_t rpb = table_rows(W, H);
+        const uint32_t rpb = g.link_general ? 0u : table_rows(W, H);
         if (!rpb) continue;   // k_tile_link handles sensors the table cannot cover
         const uint32_t nb = (H + rpb - 1) / rpb, W2 = W + 2;
         uint32_t begin, end;
@@ -870,11 +880,12 @@ cudaError_t init_kernel_attributes() {
 
 void launch_tile_border(const Work &w, const Launch &L) {
     const int smem = TILE_LINK_SMEM;
-    k_tile_link_table<<<L.fit(k_tile_link_table, TAB_THREADS, TAB_SMEM), TAB_THREADS, TAB_SMEM, L.stream>>>(w);
+    k_tile_link_table<<<L.fit(k_tile_link_table, TAB_THREADS, TAB_SMEM, G_LINK), TAB_THREADS, TAB_SMEM,
+                        L.stream>>>(w);
     L.mark("k_tile_link_table");
-    k_tile_link<<<L.fit(k_tile_link, LINK_THREADS, smem), LINK_THREADS, smem, L.stream>>>(w);
+    k_tile_link<<<L.fit(k_tile_link, LINK_THREADS, smem, G_LINK), LINK_THREADS, smem, L.stream>>>(w);
     L.mark("k_tile_link");
-    k_border_fast<<<L.fit(k_border_fast, BF_WARPS * 32, 0), BF_WARPS * 32, 0, L.stream>>>(w);
+    k_border_fast<<<L.fit(k_border_fast, BF_WARPS * 32, 0, G_LINK), BF_WARPS * 32, 0, L.stream>>>(w);
     L.mark("k_border_fast");
     k_border_link<<<L.fit(k_border_link, BORDER_THREADS, 0), BORDER_THREADS, 0, L.stream>>>(w);
     L.mark("k_border_link");

@@ -358,9 +358,9 @@ cudaError_t init_sortfast_attributes() {
 }
 
 void launch_sort_fast(const Work &w, const Launch &L) {
-    k_tile_sort<<<L.fit(k_tile_sort, LS_THREADS, LS_SMEM), LS_THREADS, LS_SMEM, L.stream>>>(w);
+    k_tile_sort<<<L.fit(k_tile_sort, LS_THREADS, LS_SMEM, G_SORT), LS_THREADS, LS_SMEM, L.stream>>>(w);
     L.mark("k_tile_sort");
-    k_tile_merge<<<L.fit(k_tile_merge, LS_THREADS, LM_SMEM), LS_THREADS, LM_SMEM, L.stream>>>(w);
+    k_tile_merge<<<L.fit(k_tile_merge, LS_THREADS, LM_SMEM, G_SORT), LS_THREADS, LM_SMEM, L.stream>>>(w);
     L.mark("k_tile_merge");
     k_sort_check<<<L.fit(k_sort_check, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_sort_check");

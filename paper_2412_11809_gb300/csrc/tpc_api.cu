@@ -130,10 +130,26 @@ struct Workspace {
     Work w{};
     DevMem mem;
 
-    // Bytes ensure(positions) allocates (the same arrays, each rounded up to
-    // 256 bytes as DevMem does).
-    static size_t bytes_for(size_t positions) {
-        const size_t need = std::max<size_t>(((positions + TILE - 1) / TILE) * TILE, TILE);
+    size_t alloc_need = 0;   // positions the arrays were sized for (whole tiles, spare tile excluded)
+
+    static size_t round_tiles(size_t positions) {
+        return std::max<size_t>(((positions + TILE - 1) / TILE) * TILE, TILE);
+    }
+
+    // Positions ensure(positions) sizes the arrays for: the need itself on
+    // the first allocation; on growth at least double the old size (at most
+    // 2^26 positions more), so that a sequence of growing steps regrows, and
+    // re-captures its graph, only a few times.
+    size_t grown(size_t positions) const {
+        const size_t need = round_tiles(positions);
+        if (!w.seg || !alloc_need) return need;
+        if (need <= alloc_need) return alloc_need;
+        return std::max(need, round_tiles(std::min(2 * alloc_need, alloc_need + (size_t(1) << 26))));
+    }
+
+    // Bytes of the arrays for `need` positions (the same arrays ensure()
+    // allocates, each rounded up to 256 bytes as DevMem does).
+    static size_t bytes_for_need(size_t need) {
         const size_t P = need + TILE, T = need / TILE + MAX_SEGS;
         auto r = [](size_t count, size_t size) { return ((std::max<size_t>(count, 1) * size) + 255) & ~size_t(255); };
         return r(MAX_SEGS, sizeof(Seg)) + r(1, sizeof(Prob)) + 3 * r(T, 4) + 5 * r(P, 4) + r(P, 2) +
@@ -141,11 +157,17 @@ struct Workspace {
                r((size_t)RADIX * T, 4) + r((size_t)MAX_SEGS * RADIX, 4);
     }
 
+    // Bytes held once ensure(positions) has run.
+    size_t bytes_after(size_t positions) const {
+        const size_t need = grown(positions);
+        return w.seg && need == alloc_need ? mem.bytes : bytes_for_need(need);
+    }
+
     cudaError_t ensure(size_t positions) {
-        size_t need = ((positions + TILE - 1) / TILE) * TILE;
-        if (need <= pos_cap && w.seg) return cudaSuccess;
+        size_t need = grown(positions);
+        if (w.seg && need == alloc_need) return cudaSuccess;
         mem.release();   // freed after the steps already queued on the owner's stream
-        need = std::max<size_t>(need, TILE);
+        alloc_need = need;
         pos_cap = need;
         tile_cap = need / TILE + MAX_SEGS;   // segments pad to whole tiles
         // segments are laid out on whole tiles, so `need` (a sum of whole
@@ -184,7 +206,7 @@ struct Workspace {
         if (e != cudaSuccess) {
             mem.release();
             w = Work{};
-            pos_cap = tile_cap = 0;
+            pos_cap = tile_cap = alloc_need = 0;
         }
         ++gen;
         return e;
@@ -302,11 +324,15 @@ struct tpc_ctx {
     cudaEvent_t stage_ev = nullptr;
     cudaEvent_t done_ev = nullptr;
 
+    // launch choices (tpc_set_tuning / tpc_tune_batch); a batch uses its lead's
+    Tuning tune{};
+
     // graph of the step sequence
     cudaGraphExec_t graph = nullptr;
     int graph_nsegs = 0;
     uint64_t graph_gen = 0;        // workspace generation the graph was captured on
     int graph_grid = 0;
+    Tuning graph_tune{};           // launch choices the graph was captured with
 
     std::mutex mu;
 
@@ -344,11 +370,20 @@ int grid_of(const tpc_ctx *c) {
     return c->sms * k;
 }
 
+// Entries ensure_out(c, n) sizes the output buffers for: n (at least 1024);
+// on growth at least double the old size (at most 2^26 entries more).
+size_t out_grown(const tpc_ctx *c, size_t n) {
+    const size_t cap = std::max<size_t>(n, 1024);
+    if (!c->d_labels || !c->out_cap) return cap;
+    if (cap <= c->out_cap) return c->out_cap;
+    return std::max(cap, std::min(2 * c->out_cap, c->out_cap + (size_t(1) << 26)));
+}
+
 cudaError_t ensure_out(tpc_ctx *c, size_t n) {
     if (n <= c->out_cap && c->d_labels) return cudaSuccess;
+    const size_t cap = out_grown(c, n);
     c->outmem.release();
     cudaError_t e = cudaSuccess;
-    size_t cap = std::max<size_t>(n, 1024);
     c->d_labels = c->outmem.alloc<uint64_t>(cap, e);
     c->d_index = c->outmem.alloc<uint64_t>(cap, e);
     c->d_rec = c->outmem.alloc<tpc_cluster>(cap, e);
@@ -391,14 +426,17 @@ void enqueue_kernels(const Work &w, int nsegs, const Launch &L) {
 // Run the fixed kernel sequence, from a CUDA graph captured on first use
 // (and re-captured when the workspace or the segment count changes).
 cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, Tracer *tr = nullptr) {
-    const Launch L{grid_of(owner), st, nullptr, owner->sms, owner->ctas_per_sm};
+    Launch L{grid_of(owner), st, nullptr, owner->sms, owner->ctas_per_sm};
+    L.tune = owner->tune;
     if (tr) {   // kernels one by one with an event after each (no graph)
         cudaEventRecord(tr->ev[0], st);
-        enqueue_kernels(ws.w, nsegs, Launch{L.grid, st, tr, owner->sms, L.cap});
+        Launch T = L;
+        T.tr = tr;
+        enqueue_kernels(ws.w, nsegs, T);
         return cudaGetLastError();
     }
     if (!owner->graph || owner->graph_nsegs != nsegs || owner->graph_gen != ws.gen ||
-        owner->graph_grid != L.grid) {
+        owner->graph_grid != L.grid || std::memcmp(&owner->graph_tune, &owner->tune, sizeof(Tuning)) != 0) {
         if (owner->graph) {
             cudaGraphExecDestroy(owner->graph);
             owner->graph = nullptr;
@@ -409,7 +447,9 @@ cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, 
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            enqueue_kernels(ws.w, nsegs, Launch{L.grid, cap_st, nullptr, owner->sms, L.cap});
+            Launch C = L;
+            C.stream = cap_st;
+            enqueue_kernels(ws.w, nsegs, C);
             e = cudaStreamEndCapture(cap_st, &g);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&owner->graph, g, 0);
@@ -422,19 +462,32 @@ cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, 
         owner->graph_nsegs = nsegs;
         owner->graph_gen = ws.gen;
         owner->graph_grid = L.grid;
+        owner->graph_tune = owner->tune;
     }
     return cudaGraphLaunch(owner->graph, st);
 }
 
-Seg base_seg(const tpc_ctx *c) {
+// Whether a sensor takes k_tile_link instead of the table kernel under the
+// launch choices t (bit 0: single-band sensors, bit 1: banded ones).
+uint32_t link_general(const Tuning &t, uint32_t W, uint32_t H) {
+    const int nb = link_bands(W, H);
+    if (nb == 1) return t.general_link & 1u;
+    if (nb > 1) return (t.general_link >> 1) & 1u;
+    return 0;
+}
+
+Seg base_seg(const tpc_ctx *c, const Tuning &t) {
     Seg s{};
     s.width = c->width;
     s.height = c->height;
     s.dt = c->dt32;
     s.variant = (uint32_t)c->variant;
     s.max_disorder = ~0ull;
+    s.link_general = link_general(t, c->width, c->height);
     return s;
 }
+
+Seg base_seg(const tpc_ctx *c) { return base_seg(c, c->tune); }
 
 cudaError_t stage_host(tpc_ctx *c, tpc_hit *dst, const tpc_hit *src, size_t n) {
     cudaPointerAttributes a{};
@@ -584,6 +637,9 @@ int read_result(tpc_ctx *c, ResultInfo &r) {
     if (cudaMemcpy(&r.seg, c->res_seg, sizeof(Seg), cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(&r.prob, c->res_prob, sizeof(Prob), cudaMemcpyDeviceToHost) != cudaSuccess)
         return TPC_ERR_CUDA;
+    // the last streaming step's open hits are the exact carry: the next push
+    // sizes its arrays from it instead of the running upper bound
+    if (c->res_streaming && c->ss && !r.prob.err && r.seg.n_open <= c->carry_ub) c->carry_ub = r.seg.n_open;
     return map_err(r.prob.err);
 }
 
@@ -683,8 +739,8 @@ int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
     if (c->max_disorder != ~0ull) {
         // streaming: copy the chunk behind the carry and cluster it now
         if (c->variant != TPC_LOCAL) return TPC_ERR_ARG;
-        if (c->budget && over_budget(c, Workspace::bytes_for(c->carry_ub + n) > c->ws.mem.bytes
-                                            ? Workspace::bytes_for(c->carry_ub + n) - c->ws.mem.bytes : 0))
+        if (c->budget && over_budget(c, c->ws.bytes_after(c->carry_ub + n) > c->ws.mem.bytes
+                                            ? c->ws.bytes_after(c->carry_ub + n) - c->ws.mem.bytes : 0))
             return TPC_ERR_BUSY;
         int rc = ensure_stream_buffers(c, n);
         if (rc) return rc;
@@ -732,7 +788,8 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
     if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
     const Work &w = c->ws.w;
     const VarWork &v = c->vs.v;
-    const Launch L{grid_of(c), c->stream, tr, c->sms, c->ctas_per_sm};
+    Launch L{grid_of(c), c->stream, tr, c->sms, c->ctas_per_sm};
+    L.tune = c->tune;
     if (tr) cudaEventRecord(tr->ev[0], c->stream);
     launch_setup(w, 1, L);
     launch_sort_fast(w, L);
@@ -786,7 +843,7 @@ static int flush_impl(tpc_ctx *c, Tracer *tr) {
     if (c->variant != TPC_LOCAL) return flush_variant(c, tr);
     const size_t n = c->pending;
     c->has_result = false;   // the workspace may move: the last result is gone
-    if (over_budget(c, Workspace::bytes_for(n) > c->ws.mem.bytes ? Workspace::bytes_for(n) - c->ws.mem.bytes : 0))
+    if (over_budget(c, c->ws.bytes_after(n) > c->ws.mem.bytes ? c->ws.bytes_after(n) - c->ws.mem.bytes : 0))
         return TPC_ERR_BUSY;
     if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
     if (ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
@@ -913,16 +970,21 @@ int tpc_cluster_features(tpc_ctx *c, tpc_cluster *out, size_t cap, size_t *n_out
     return cudaStreamSynchronize(c->stream) == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }
 
-int tpc_batch_flush(tpc_ctx **ctxs, int n) {
+}  // extern "C"
+
+int tpc::check_batch(tpc_ctx **ctxs, int n) {
     if (!ctxs || n <= 0 || n > MAX_SEGS) return TPC_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || ctxs[i]->max_disorder != ~0ull || ctxs[i]->variant != TPC_LOCAL) return TPC_ERR_ARG;
         for (int j = 0; j < i; ++j) if (ctxs[j] == ctxs[i]) return TPC_ERR_ARG;
         if (ctxs[i]->device != ctxs[0]->device) return TPC_ERR_ARG;
     }
+    return TPC_OK;
+}
+
+int tpc::batch_step(tpc_ctx **ctxs, int n, bool consume) {
     tpc_ctx *lead = ctxs[0];
-    std::vector<std::unique_lock<std::mutex>> locks;
-    for (int i = 0; i < n; ++i) locks.emplace_back(ctxs[i]->mu);
+    const Tuning &t = lead->tune;
     for (int i = 0; i < n; ++i) ctxs[i]->has_result = false;   // workspaces may move
     size_t positions = 0;
     for (int i = 0; i < n; ++i) positions += ((ctxs[i]->pending + TILE - 1) / TILE) * TILE;
@@ -937,24 +999,31 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
             return TPC_ERR_CUDA;
     }
     if (lead->ws.ensure(positions) != cudaSuccess) return TPC_ERR_NOMEM;
+    // segment order: as given, or (a tuning choice) most pending hits first,
+    // so that the big sensors' tiles start in the first wave
+    std::vector<int> perm(n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    if (t.order == 1)
+        std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return ctxs[a]->pending > ctxs[b]->pending; });
     std::vector<Seg> segs(n);
-    for (int i = 0; i < n; ++i) {
-        tpc_ctx *c = ctxs[i];
-        Seg s = base_seg(c);
+    for (int k = 0; k < n; ++k) {
+        tpc_ctx *c = ctxs[perm[k]];
+        Seg s = base_seg(c, t);
         s.hits = c->zc ? c->zc : c->in;
         s.out_labels = c->d_labels;
         s.out_rec = c->d_rec;
         s.out_cap = (uint32_t)c->out_cap;
         s.gidx_base = c->pushed;
         s.n_new = (uint32_t)c->pending;
-        segs[i] = s;
+        segs[k] = s;
     }
     if (upload_segs(lead, lead->ws.w, segs.data(), n, lead->stream) != cudaSuccess) return TPC_ERR_CUDA;
     if (run_step(lead, lead->ws, n, lead->stream) != cudaSuccess) return TPC_ERR_CUDA;
-    for (int i = 0; i < n; ++i) {   // each context keeps its own copy of its results
-        if (cudaMemcpyAsync(ctxs[i]->own_res_seg, lead->ws.w.seg + i, sizeof(Seg), cudaMemcpyDeviceToDevice,
+    for (int k = 0; k < n; ++k) {   // each context keeps its own copy of its results
+        tpc_ctx *c = ctxs[perm[k]];
+        if (cudaMemcpyAsync(c->own_res_seg, lead->ws.w.seg + k, sizeof(Seg), cudaMemcpyDeviceToDevice,
                             lead->stream) != cudaSuccess ||
-            cudaMemcpyAsync(ctxs[i]->own_res_prob, lead->ws.w.prob, sizeof(Prob), cudaMemcpyDeviceToDevice,
+            cudaMemcpyAsync(c->own_res_prob, lead->ws.w.prob, sizeof(Prob), cudaMemcpyDeviceToDevice,
                             lead->stream) != cudaSuccess)
             return TPC_ERR_CUDA;
     }
@@ -962,6 +1031,7 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
     for (int i = 0; i < n; ++i) {
         tpc_ctx *c = ctxs[i];
         if (i && cudaStreamWaitEvent(c->stream, lead->done_ev, 0) != cudaSuccess) return TPC_ERR_CUDA;
+        if (!consume) continue;   // a tuning trial: the hits stay pending
         c->res_base = c->pushed;
         c->pushed += c->pending;
         c->pending = 0;
@@ -972,6 +1042,16 @@ int tpc_batch_flush(tpc_ctx **ctxs, int n) {
         c->res_streaming = false;
     }
     return TPC_OK;
+}
+
+extern "C" {
+
+int tpc_batch_flush(tpc_ctx **ctxs, int n) {
+    int rc = check_batch(ctxs, n);
+    if (rc) return rc;
+    std::vector<std::unique_lock<std::mutex>> locks;
+    for (int i = 0; i < n; ++i) locks.emplace_back(ctxs[i]->mu);
+    return batch_step(ctxs, n, true);
 }
 
 int tpc_forest(tpc_ctx *c, uint32_t *parent, uint32_t *input_pos, size_t cap, size_t *n_out) {
@@ -1017,9 +1097,9 @@ size_t tpc::ctx_projected_bytes(tpc_ctx *c, size_t n) {
     }
     const size_t stream_bytes = 2 * (carry_cap + chunk_cap) * (sizeof(tpc_hit) + sizeof(uint64_t));
     const size_t positions = c->carry_ub + n;
-    const size_t ws = positions <= c->ws.pos_cap && c->ws.w.seg ? c->ws.mem.bytes : Workspace::bytes_for(positions);
-    const size_t out_n = std::max<size_t>(positions, 1024);
-    const size_t out = out_n <= c->out_cap && c->d_labels ? c->outmem.bytes
+    const size_t ws = c->ws.bytes_after(positions);
+    const size_t out_n = out_grown(c, positions);
+    const size_t out = out_n == c->out_cap && c->d_labels ? c->outmem.bytes
                                                           : 2 * ((out_n * 8 + 255) & ~size_t(255)) +
                                                                 ((out_n * sizeof(tpc_cluster) + 255) & ~size_t(255));
     return ws + out + stream_bytes + c->in_cap * sizeof(tpc_hit);
@@ -1034,7 +1114,7 @@ void tpc::ctx_release_scratch(tpc_ctx *c) {
     std::lock_guard<std::mutex> lk(c->mu);
     c->ws.mem.release();   // stream-ordered: after the context's queued work
     c->ws.w = Work{};
-    c->ws.pos_cap = c->ws.tile_cap = 0;
+    c->ws.pos_cap = c->ws.tile_cap = c->ws.alloc_need = 0;
     ++c->ws.gen;
     c->outmem.release();
     c->d_labels = c->d_index = nullptr;
@@ -1058,6 +1138,14 @@ int tpc::ctx_settle(tpc_ctx *c) {
 }
 
 cudaStream_t tpc::ctx_stream(tpc_ctx *c) { return c->stream; }
+Tuning &tpc::ctx_tuning(tpc_ctx *c) { return c->tune; }
+std::mutex &tpc::ctx_mutex(tpc_ctx *c) { return c->mu; }
+size_t tpc::ctx_pending(tpc_ctx *c) { return c->pending; }
+void tpc::ctx_sensor(tpc_ctx *c, uint32_t *width, uint32_t *height) {
+    *width = c->width;
+    *height = c->height;
+}
+int tpc::ctx_device(tpc_ctx *c) { return c->device; }
 
 extern "C" {
 

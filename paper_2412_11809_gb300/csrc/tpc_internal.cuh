@@ -84,7 +84,8 @@ struct Seg {
     uint32_t n_final;          // hits finalised
     uint32_t n_clusters;       // clusters finalised
     uint32_t n_open;           // hits carried forward
-    uint32_t pad1;
+    uint32_t link_general;     // set by the host (a tuning choice): link every tile with
+                               // k_tile_link instead of the shared-memory table kernel
 };
 
 struct Prob {
@@ -287,22 +288,36 @@ struct Tracer {
 // shared memory (registers included); cached per device.
 int occupancy(const void *kernel, int threads, size_t smem);
 
+// Launch choices a tuner may change (tpc_tuning at the ABI): CTAs per SM of
+// each group of persistent kernels and the feature kernel's span.  Results
+// never depend on them.
+enum TuneGroup { G_SORT = 0, G_LINK = 1, G_ACC = 2, G_OUT = 3, NGROUPS = 4 };
+struct Tuning {
+    uint8_t cap[NGROUPS] = {0, 0, 0, 0};   // CTAs per SM per group, 0 = as many as fit
+    uint16_t acc_span = 1024;              // k_accumulate positions per pass: 512, 1024, 2048
+    uint8_t general_link = 0;              // bit 0: single-band sensors, bit 1: banded sensors
+                                           // take k_tile_link instead of the table kernel
+    uint8_t order = 0;                     // 1: batch segments largest first
+};
+
 struct Launch {
     int grid;          // fallback grid when the SM count is unknown
     cudaStream_t stream;
     Tracer *tr = nullptr;
     int sms = 0;       // SM count
     int cap = 0;       // at most this many CTAs per SM (0 = as many as fit)
+    Tuning tune{};
     void mark(const char *name) const { if (tr) tr->mark(name, stream); }
     // Grid of a persistent kernel (a strided loop over tiles): exactly one
-    // wave, every SM filled to the kernel's occupancy.  A grid that is not a
-    // whole multiple of the resident CTAs would leave a partial second wave
-    // running on a fraction of each SM.
+    // wave, every SM filled to the kernel's occupancy (or to its group's
+    // tuned cap).  A grid that is not a whole multiple of the resident CTAs
+    // would leave a partial second wave running on a fraction of each SM.
     template <class K>
-    int fit(K *kernel, int threads, size_t smem) const {
+    int fit(K *kernel, int threads, size_t smem, int group = -1) const {
         if (sms <= 0) return grid;
         int per_sm = occupancy(reinterpret_cast<const void *>(kernel), threads, smem);
         if (cap > 0 && per_sm > cap) per_sm = cap;
+        if (group >= 0 && tune.cap[group] > 0 && per_sm > tune.cap[group]) per_sm = tune.cap[group];
         return sms * (per_sm > 0 ? per_sm : 1);
     }
 };
@@ -317,6 +332,7 @@ void launch_radix_pass(const Work &w, int pass, const Launch &L);
 void launch_gather(const Work &w, const Launch &L);
 void launch_link(const Work &w, const Launch &L);          // tile + border + flatten
 void launch_tile_border(const Work &w, const Launch &L);
+int link_bands(uint32_t W, uint32_t H);   // table bands of a sensor, 0 = general link kernel
 void launch_flatten(const Work &w, const Launch &L);
 void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const Launch &L);
 Work variant_view(const Work &w, const VarWork &v);
