@@ -257,6 +257,24 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+def forest_depth(parent: np.ndarray) -> dict:
+    """Depth of every node of a union-find forest (steps to its root), as
+    the step left it: the forest after the link kernels' finds, which halve
+    paths as they go, and the feature kernel's finds."""
+    cur = np.arange(len(parent), dtype=np.int64)
+    par = parent.astype(np.int64)
+    depth = np.zeros(len(parent), dtype=np.int32)
+    active = np.flatnonzero(par[cur] != cur)
+    while len(active):
+        depth[active] += 1
+        cur[active] = par[cur[active]]
+        active = active[par[cur[active]] != cur[active]]
+    roots = int(np.count_nonzero(par == np.arange(len(par))))
+    return {"max": int(depth.max()) if len(depth) else 0, "mean": float(depth.mean()) if len(depth) else 0.0,
+            "nodes": int(len(parent)), "roots": roots,
+            "deeper_than_1": int(np.count_nonzero(depth > 1))}
+
+
 def oracle_sample(hits, n_sample: int, start: int = 0):
     """Time the CPU oracle (labels + features) on n_sample consecutive hits
     starting at `start`."""
@@ -397,8 +415,17 @@ def run_serving(args, dev, torch):
         done_first = {}   # (stream, j) -> (indices, labels) of the first replay, for the straddle count
 
         def waiter():
+            from paper_2412_11809_gb300 import TpcError
+            deadline = time.perf_counter() + 120
             for _ in range(len(events)):
-                r = srv.wait_raw(timeout_s=300)
+                r = None
+                while r is None and time.perf_counter() < deadline:
+                    try:
+                        r = srv.wait_raw(timeout_s=1.0)
+                    except TpcError as e:   # nothing submitted yet: the arrivals are still coming
+                        if e.name != "TPC_ERR_STATE":
+                            raise
+                        time.sleep(2e-4)
                 if r is None:
                     results.append(None)
                     return
@@ -420,7 +447,8 @@ def run_serving(args, dev, torch):
                 time.sleep(delay)
             with lock:
                 while not free_out:
-                    lock.wait()
+                    if not th.is_alive() or not lock.wait(timeout=60):
+                        raise RuntimeError("serving: no output buffers came back within 60 s")
                 lab, idx, rec = free_out.pop()
             tag = k * (1 << 20) + j
             slots[tag] = (lab, idx, rec)
@@ -700,6 +728,11 @@ def run_gpu(args):
         for name, kms in rows:
             prof.setdefault(name, []).append(kms)
     prof_ms = {k: statistics.median(v) for k, v in prof.items()}
+    try:   # union-find depth of the last profiled step's forest (SURVEY metrics)
+        parent, _ = c.forest()
+        depth = forest_depth(parent)
+    except Exception as e:   # reported, never fatal
+        depth = {"error": f"{type(e).__name__}: {e}"}
     dominant = max(prof_ms, key=prof_ms.get)
     peak, peak_src = measured_peak_gbs()
     dom_bytes = KERNEL_BYTES_PER_HIT.get(dominant, 0) * n
@@ -830,6 +863,7 @@ def run_gpu(args):
                                 "traffic": stored_traffic(dominant, n)},
             "issue_roofline": issue,
             "kernel_ms": prof_ms,
+            "forest_depth": depth,
             "cpu_baseline": cpu,
             "cpu_parallel": cpu_par,
             "e2e": {"value": e2e_value, "unit": "hits/s", "h2d_bytes_per_step": 16 * n,

@@ -254,6 +254,19 @@ int tpc_profile_flush(tpc_ctx *ctx, const char **names, float *ms, int cap, int 
    Section 4.1, and each root is its cluster's earliest hit. */
 int tpc_forest(tpc_ctx *ctx, uint32_t *parent, uint32_t *input_pos, size_t cap, size_t *n_out);
 
+/* Diagnostics of the context's last TPC_GLOBAL or TPC_STATIC flush (zero
+   otherwise): (b) rounds of merges on the device, of which full passes over
+   every hit (the first, and any after the list of open edges overflowed),
+   and exact recomputations of the groups' last ToA; (c) components longer
+   than the shared-memory staging, swept through its sliding window, and of
+   those the ones swept again from global memory (more hits within dt than
+   the window holds).  Waits for the context's work. */
+typedef struct tpc_variant_stats {
+    uint32_t rounds, full_rounds, exact_checks;
+    uint32_t windowed, window_fallbacks;
+} tpc_variant_stats;
+int tpc_variant_stats_get(tpc_ctx *ctx, tpc_variant_stats *out);
+
 /* Bytes of device memory the context currently holds. */
 int tpc_device_bytes(tpc_ctx *ctx, size_t *bytes);
 

@@ -74,7 +74,9 @@ typedef struct {
     uint64_t *idx;     /* n hit indices grouped by pixel */
 } pixel_lists;
 
-static const or_hit *g_sort_hits;   /* qsort has no context argument */
+/* qsort has no context argument; one per thread, so that calls from
+   several threads (the full-size tests run two at once) do not mix */
+static _Thread_local const or_hit *g_sort_hits;
 
 static int cmp_toa_idx(const void *a, const void *b) {
     uint64_t i = *(const uint64_t *)a, j = *(const uint64_t *)b;

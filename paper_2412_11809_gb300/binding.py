@@ -71,6 +71,7 @@ SIGNATURES = {
     "tpc_tune_batch": ([ctypes.POINTER(_VP), _INT, ctypes.c_char_p, _INT, _VP], _INT),
     "tpc_tune_cache_lookup": ([ctypes.c_char_p, ctypes.c_char_p, _VP, ctypes.POINTER(ctypes.c_double)], _INT),
     "tpc_tune_cache_store": ([ctypes.c_char_p, ctypes.c_char_p, _VP, ctypes.c_double], _INT),
+    "tpc_variant_stats_get": ([_VP, _VP], _INT),
     "tpc_strerror": ([_INT], ctypes.c_char_p),
     "tpc_destroy": ([_VP], None),
 }
@@ -325,6 +326,12 @@ class Clusterer:
         t = Tuning()
         _check(self._lib.tpc_get_tuning(self._h, ctypes.byref(t)), "tpc_get_tuning")
         return t
+
+    def variant_stats(self) -> dict:
+        """``tpc_variant_stats_get``: diagnostics of the last (b)/(c) flush."""
+        st = (ctypes.c_uint32 * 5)()
+        _check(self._lib.tpc_variant_stats_get(self._h, st), "tpc_variant_stats_get")
+        return dict(zip(("rounds", "full_rounds", "exact_checks", "windowed", "window_fallbacks"), st))
 
     def device_bytes(self) -> int:
         b = ctypes.c_size_t()

@@ -230,7 +230,12 @@ struct VarSpace {
         v.glast = mem.alloc<uint32_t>(positions, e);
         v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
         v.latest = mem.alloc<uint32_t>(9 * positions, e);
-        v.changed = mem.alloc<uint32_t>(1, e);
+        v.changed = mem.alloc<uint32_t>(4, e);
+        // open (b) edges: 4 per position per list; a round that finds more
+        // marks the overflow and the next round reads every hit's 9 again
+        v.edge_cap = (uint32_t)std::min<size_t>(4 * positions, 0xFFFFFFFFull);
+        v.edges[0] = mem.alloc<uint2>(v.edge_cap, e);
+        v.edges[1] = mem.alloc<uint2>(v.edge_cap, e);
         v.work = mem.alloc<uint32_t>(1, e);
         v.prob = mem.alloc<Prob>(1, e);
         if (e != cudaSuccess) {
@@ -326,6 +331,8 @@ struct tpc_ctx {
 
     // launch choices (tpc_set_tuning / tpc_tune_batch); a batch uses its lead's
     Tuning tune{};
+    tpc_variant_stats vstats{};    // the last (b)/(c) flush (tpc_variant_stats)
+    bool vstats_pending = false;   // (c) counters still in h_flag
 
     // graph of the step sequence
     cudaGraphExec_t graph = nullptr;
@@ -776,7 +783,7 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
     if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
     if (c->vs.ensure(c->ws.pos_cap, (size_t)c->width * c->height) != cudaSuccess) return TPC_ERR_NOMEM;
     if (ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
-    if (!c->h_flag && host_alloc(&c->fail_alloc, (void **)&c->h_flag, sizeof(uint32_t)) != cudaSuccess)
+    if (!c->h_flag && host_alloc(&c->fail_alloc, (void **)&c->h_flag, 4 * sizeof(uint32_t)) != cudaSuccess)
         return TPC_ERR_NOMEM;
     Seg s = base_seg(c);
     s.hits = c->zc ? c->zc : c->in;
@@ -804,18 +811,47 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
         launch_variant_keys(w, v, 0, L);
         for (int pass = 0; pass < 4; ++pass) launch_radix_pass(wv, pass, L);
         launch_static_sweep(w, v, L);
+        c->vstats = tpc_variant_stats{};
+        if (cudaMemcpyAsync(c->h_flag, v.changed, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess)
+            return TPC_ERR_CUDA;
+        c->vstats_pending = true;   // read at tpc_variant_stats, after the stream
     } else {
         launch_variant_keys(w, v, 1, L);
         for (int pass = 0; pass < 3; ++pass) launch_radix_pass(wv, pass, L);
         launch_pixel_timelines(w, v, c->width * c->height, L);
+        // Rounds of the rule until the partition is closed under it: the
+        // first over every hit's 9 latest neighbours, the later ones over the
+        // edges left open (all hits again after an overflow of the list);
+        // the groups' last keys are exact at the start and kept at the roots
+        // by the unions (never above the exact value), and recomputed exactly
+        // when a round merges nothing: the end is a round without merges on
+        // exact values.
+        launch_group_last(w, v, L);
+        bool full = true, exact = true;
+        int in = 0;
+        c->vstats = tpc_variant_stats{};
+        c->vstats_pending = false;
         for (int round = 0;; ++round) {
             if (round > 4096) return TPC_ERR_TIMEOUT;
-            launch_global_round(w, v, L);
-            if (cudaMemcpyAsync(c->h_flag, v.changed, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
+            launch_global_edges(w, v, full, in, L);
+            ++c->vstats.rounds;
+            if (full) ++c->vstats.full_rounds;
+            if (cudaMemcpyAsync(c->h_flag, v.changed, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
                     cudaSuccess ||
                 cudaStreamSynchronize(c->stream) != cudaSuccess)
                 return TPC_ERR_CUDA;
-            if (!*c->h_flag) break;
+            const bool merged = c->h_flag[0] != 0, overflow = c->h_flag[1] != 0;
+            in = full ? 0 : 1 - in;   // the list just written
+            full = overflow;
+            if (merged) {
+                exact = false;
+                continue;
+            }
+            if (exact) break;
+            launch_group_last(w, v, L);
+            ++c->vstats.exact_checks;
+            exact = true;
         }
     }
     launch_flatten(w, L);
@@ -1148,6 +1184,19 @@ void tpc::ctx_sensor(tpc_ctx *c, uint32_t *width, uint32_t *height) {
 int tpc::ctx_device(tpc_ctx *c) { return c->device; }
 
 extern "C" {
+
+int tpc_variant_stats_get(tpc_ctx *c, tpc_variant_stats *out) {
+    if (!c || !out) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->vstats_pending) {
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+        c->vstats.windowed = c->h_flag[0];
+        c->vstats.window_fallbacks = c->h_flag[1];
+        c->vstats_pending = false;
+    }
+    *out = c->vstats;
+    return TPC_OK;
+}
 
 int tpc_device_bytes(tpc_ctx *c, size_t *bytes) {
     if (!c || !bytes) return TPC_ERR_ARG;

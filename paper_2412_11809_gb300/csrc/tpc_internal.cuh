@@ -143,7 +143,10 @@ struct VarWork {
     uint32_t *glast;           // (b): per root, last key of its group
     uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
     uint32_t *latest;          // (b): per position, 9 slots: latest earlier hit on each neighbour pixel
-    uint32_t *changed;         // (b): a round merged something
+    uint32_t *changed;         // (b): [0] a round merged something, [1] the edge list overflowed,
+                               //      [2], [3] entries in edge lists 0 and 1
+    uint2 *edges[2];           // (b): edges (hit, latest neighbour) not merged yet, ping-pong
+    uint32_t edge_cap;         // (b): entries each edge list holds
     uint32_t *work;            // (c): next chunk of the grouped order to sweep
     Prob *prob;                // problem view of the grouping sort
 };
@@ -338,7 +341,8 @@ void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const La
 Work variant_view(const Work &w, const VarWork &v);
 void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L);
 void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, const Launch &L);
-void launch_global_round(const Work &w, const VarWork &v, const Launch &L);
+void launch_group_last(const Work &w, const VarWork &v, const Launch &L);
+void launch_global_edges(const Work &w, const VarWork &v, int full, int in_list, const Launch &L);
 void launch_features(const Work &w, const Launch &L);
 void launch_outputs(const Work &w, const Launch &L);
 

@@ -17,8 +17,11 @@
 // The sweep's result is therefore the least partition, reached from the (a)
 // components by merging, in which hit h is joined to L = the latest earlier
 // hit on each of its 9 pixels whenever toa(h) <= last(group(L)) + dt.
-// Rounds apply that rule with the groups' last ToA taken at the start of the
-// round (stale values only postpone merges) until a round merges nothing.
+// Rounds apply that rule: the first to every hit's 9 latest neighbours, the
+// later ones to the edges still open, with the groups' last ToA kept at the
+// roots by the unions (a lagging value only postpones a merge) and
+// recomputed exactly when a round merges nothing; the partition is final
+// after a round without merges on exact values.
 // Per-pixel timelines come from a stable radix sort of the hits by pixel.
 #include "tpc_internal.cuh"
 
@@ -130,6 +133,96 @@ __device__ void sweep_component(const SweepView<STAGED> &V, uint32_t n, uint32_t
     }
 }
 
+// Components of more than SW_CAP hits: the same sweep over a sliding window
+// of the component's last SW_CAP hits in shared memory (slot = index mod
+// SW_CAP).  A (c) cluster spans at most dt, so while every hit within dt of
+// the hit being swept is still in the window, a hit that leaves it belongs
+// to a cluster that is closed for every later hit: its root is final.  On
+// leaving, its root goes to global memory (cpar, by component index, and
+// the parent array); finds that reach a hit that has left read it there.  A
+// batch of 32 hits enters every 32 steps, pushing the 32 oldest out; if one
+// of those is within dt of the first newcomer, the window is too small and
+// the component is swept again from global memory (returns false).
+struct WindowView {
+    uint32_t *wk, *wp, *wc;    // window: key, pixel, parent (component index)
+    uint32_t *cpar;            // global: final root of each hit that left
+    uint32_t lo;               // first component index still in the window
+    __device__ uint32_t key(uint32_t i) const { return wk[i % SW_CAP]; }
+    __device__ uint32_t pix(uint32_t i) const { return wp[i % SW_CAP]; }
+    __device__ uint32_t find(uint32_t x) const {
+        volatile uint32_t *c = wc;
+        while (true) {
+            if (x < lo) return *reinterpret_cast<volatile uint32_t *>(&cpar[x]);
+            const uint32_t p = c[x % SW_CAP];
+            if (p == x) return x;
+            if (p < lo) return *reinterpret_cast<volatile uint32_t *>(&cpar[p]);
+            const uint32_t gp = c[p % SW_CAP];
+            if (gp == p) return p;
+            c[x % SW_CAP] = gp;
+            x = gp;
+        }
+    }
+};
+
+__device__ bool sweep_windowed(WindowView V, const uint32_t *skey, const uint32_t *spix, const uint32_t *gv,
+                               uint32_t *parent, uint32_t q0, uint32_t n, uint32_t dt, int lane) {
+    for (uint32_t i = 0; i < n; ++i) {
+        if ((i & 31u) == 0) {   // hits [i, i + 32) enter, [i - SW_CAP, i - SW_CAP + 32) leave
+            const uint32_t ki = skey[gv[q0 + i]];
+            if (i >= SW_CAP) {
+                const uint32_t j = i - SW_CAP + lane;   // < i <= n - 1
+                if (__any_sync(0xffffffffu, ki - V.key(j) <= dt)) return false;
+                const uint32_t r = V.find(j);
+                __syncwarp();
+                V.cpar[j] = r;
+                parent[gv[q0 + j]] = gv[q0 + r];
+                __syncwarp();
+                V.lo = i - SW_CAP + 32;
+            }
+            const uint32_t e = i + lane;
+            if (e < n) {
+                const uint32_t se = gv[q0 + e];
+                V.wk[e % SW_CAP] = skey[se];
+                V.wp[e % SW_CAP] = spix[se];
+                V.wc[e % SW_CAP] = e;
+            }
+            __syncwarp();
+        }
+        if (i == 0) continue;
+        const uint32_t ki = V.key(i), pi = V.pix(i);
+        uint32_t root = 0xFFFFFFFFu;   // the earliest open root joined so far
+        for (uint32_t base = 0; base < i; base += 32) {
+            const bool valid = base + lane < i && i - 1 - base - lane >= V.lo;
+            const uint32_t j = valid ? i - 1 - base - lane : i;
+            const bool in = valid && ki - V.key(j) <= dt;
+            if (!__any_sync(0xffffffffu, in)) break;   // keys only fall further back
+            uint32_t r = 0xFFFFFFFFu;
+            if (in && adjacent_v(pi, V.pix(j))) {
+                const uint32_t rj = V.find(j);
+                if (rj >= V.lo && ki - V.key(rj) <= dt) r = rj;   // that cluster is still open
+            }
+            const uint32_t m = __reduce_min_sync(0xffffffffu, r);
+            __syncwarp();
+            if (m != 0xFFFFFFFFu) {
+                const uint32_t target = m < root ? m : root;
+                if (r != 0xFFFFFFFFu && r != target) V.wc[r % SW_CAP] = target;
+                if (lane == 0 && root != 0xFFFFFFFFu && root != target) V.wc[root % SW_CAP] = target;
+                root = target;
+            }
+            __syncwarp();
+        }
+        if (lane == 0 && root != 0xFFFFFFFFu) V.wc[i % SW_CAP] = root;
+        __syncwarp();
+    }
+    // the hits still in the window
+    const uint32_t first = V.lo;
+    for (uint32_t j = first + lane; j < n; j += 32) {
+        const uint32_t r = V.find(j);
+        parent[gv[q0 + j]] = gv[q0 + r];
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(SW_WARPS * 32) k_static_sweep(Work w, VarWork v) {
     __shared__ uint32_t s_k[SW_WARPS][SW_CAP], s_p[SW_WARPS][SW_CAP], s_c[SW_WARPS][SW_CAP];
     const Prob &P = *w.prob;
@@ -173,9 +266,15 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_static_sweep(Work w, VarWork 
                 sweep_component(V, n, dt, lane);
                 for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
             } else {
-                const SweepView<false> V{nullptr, nullptr, v.cpar + q0, skey, w.spix, gv, q0};
-                sweep_component(V, n, dt, lane);
-                for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
+                const WindowView WV{s_k[warp], s_p[warp], s_c[warp], v.cpar + q0, 0};
+                if (lane == 0) atomicAdd(&v.changed[0], 1u);   // diagnostics: windowed components
+                if (!sweep_windowed(WV, skey, w.spix, gv, w.parent, q0, n, dt, lane)) {
+                    if (lane == 0) atomicAdd(&v.changed[1], 1u);   // ... and those swept again
+                    __syncwarp();   // more than the window within dt: from global memory
+                    const SweepView<false> V{nullptr, nullptr, v.cpar + q0, skey, w.spix, gv, q0};
+                    sweep_component(V, n, dt, lane);
+                    for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
+                }
             }
             __syncwarp();   // the staging is rewritten for the next component
         }
@@ -284,8 +383,59 @@ __global__ void __launch_bounds__(256) k_group_last(Work w, VarWork v) {
     }
 }
 
-// (b): one round of merges along (h, latest earlier hit on each 9-pixel).
-__global__ void __launch_bounds__(256) k_global_round(Work w, VarWork v) {
+// (b) with the groups' last keys kept at their roots during the unions: when
+// root b is hooked under a, a's last key takes b's (atomicMax).  A value can
+// lag behind its group's (a concurrent hook of a loses it), never exceed it,
+// so every union made on it is one the sweep makes; an exact recomputation
+// when a round merges nothing decides the end.
+__device__ __forceinline__ void gunion_last(uint32_t *parent, uint32_t *glast, uint32_t a, uint32_t b) {
+    while (true) {
+        a = gfind(parent, a);
+        b = gfind(parent, b);
+        if (a == b) return;
+        if (a > b) { const uint32_t t = a; a = b; b = t; }
+        if (atomicCAS(parent + b, b, a) == b) {
+            const uint32_t lb = *reinterpret_cast<volatile uint32_t *>(&glast[b]);
+            if (*reinterpret_cast<volatile uint32_t *>(&glast[a]) < lb) atomicMax(&glast[a], lb);
+            return;
+        }
+    }
+}
+
+// Apply the rule to one edge (hit s, latest earlier hit l on one of its 9
+// pixels); returns 1 if merged, 0 if the groups already agree, 2 if the
+// edge stays open (its groups differ and the rule does not hold yet).
+__device__ __forceinline__ int global_edge(const Work &w, const VarWork &v, const uint32_t *skey, uint32_t dt,
+                                           uint32_t s, uint32_t l) {
+    const uint32_t rl = gfind(w.parent, l), rh = gfind(w.parent, s);
+    if (rl == rh) return 0;
+    const uint32_t last = *reinterpret_cast<volatile uint32_t *>(&v.glast[rl]);
+    if ((uint64_t)skey[s] <= (uint64_t)last + dt) {
+        gunion_last(w.parent, v.glast, s, l);
+        return 1;
+    }
+    return 2;
+}
+
+// Append the warp's open edges to list `out` (one atomic per warp); on
+// overflow the list is marked and the next round takes every hit again.
+__device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep, uint32_t s, uint32_t l) {
+    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(&v.changed[2 + out], (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    const uint32_t slot = base + __popc(m & ((1u << lane) - 1u));
+    if (keep) {
+        if (slot < v.edge_cap) v.edges[out][slot] = make_uint2(s, l);
+        else v.changed[1] = 1u;
+    }
+}
+
+// A round over every hit's 9 latest neighbours (the first round, and any
+// round after an overflow): merges what the rule allows, lists the rest.
+__global__ void __launch_bounds__(256) k_global_full(Work w, VarWork v, int out) {
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
     const uint32_t *skey = w.keys[sorted_sel(P)];
@@ -295,24 +445,61 @@ __global__ void __launch_bounds__(256) k_global_round(Work w, VarWork v) {
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         const uint32_t dt = g.dt;
-        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
-            const uint32_t key = skey[s];
-            uint32_t rh = gfind(w.parent, s);
-#pragma unroll
+        for (uint32_t s0 = begin; s0 < end; s0 += blockDim.x) {   // whole warps: the ballots below
+            const uint32_t s = s0 + threadIdx.x;
+            const bool valid = s < end;
+#pragma unroll 1
             for (int n = 0; n < 9; ++n) {
-                const uint32_t L = v.latest[(size_t)s * 9 + n];
-                if (L == 0xFFFFFFFFu) continue;
-                const uint32_t rl = gfind(w.parent, L);
-                if (rl == rh) continue;
-                if ((uint64_t)key <= (uint64_t)v.glast[rl] + dt) {
-                    gunion(w.parent, s, L);
-                    rh = gfind(w.parent, s);
-                    changed = true;
-                }
+                const uint32_t l = valid ? v.latest[(size_t)s * 9 + n] : 0xFFFFFFFFu;
+                int r = 0;
+                if (l != 0xFFFFFFFFu) r = global_edge(w, v, skey, dt, s, l);
+                changed |= r == 1;
+                push_edges(v, out, r == 2, s, l);
             }
         }
     }
-    if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(v.changed, 1u);
+    if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&v.changed[0], 1u);
+}
+
+// A round over the open edges of list `in` only.
+__global__ void __launch_bounds__(256) k_global_list(Work w, VarWork v, int in) {
+    const Prob &P = *w.prob;
+    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t dt = w.seg[0].dt;
+    const uint32_t n = v.changed[2 + in];
+    const uint32_t cnt = n < v.edge_cap ? n : v.edge_cap;
+    bool changed = false;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < cnt; e0 += stride) {
+        const uint32_t e = e0 + threadIdx.x;
+        const bool valid = e < cnt;
+        const uint2 ed = valid ? v.edges[in][e] : make_uint2(0, 0);
+        const int r = valid ? global_edge(w, v, skey, dt, ed.x, ed.y) : 0;
+        changed |= r == 1;
+        push_edges(v, 1 - in, r == 2, ed.x, ed.y);
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&v.changed[0], 1u);
+}
+
+void launch_group_last(const Work &w, const VarWork &v, const Launch &L) {
+    k_group_last_reset<<<L.fit(k_group_last_reset, 256, 0), 256, 0, L.stream>>>(w, v);
+    k_group_last<<<L.fit(k_group_last, 256, 0), 256, 0, L.stream>>>(w, v);
+    L.mark("k_group_last");
+}
+
+// One round: list `1 - in` (or, if full, every hit) into list `in`'s
+// partner.  full: out = list 0 after reading every hit.
+void launch_global_edges(const Work &w, const VarWork &v, int full, int in, const Launch &L) {
+    const int out = full ? 0 : 1 - in;
+    cudaMemsetAsync(v.changed, 0, 2 * sizeof(uint32_t), L.stream);
+    cudaMemsetAsync(v.changed + 2 + out, 0, sizeof(uint32_t), L.stream);
+    if (full) {
+        k_global_full<<<L.fit(k_global_full, 256, 0), 256, 0, L.stream>>>(w, v, out);
+        L.mark("k_global_full");
+    } else {
+        k_global_list<<<L.fit(k_global_list, 256, 0), 256, 0, L.stream>>>(w, v, in);
+        L.mark("k_global_list");
+    }
 }
 
 void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const Launch &L) {
@@ -332,6 +519,7 @@ Work variant_view(const Work &w, const VarWork &v) {
 
 void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L) {
     cudaMemsetAsync(v.work, 0, sizeof(uint32_t), L.stream);
+    cudaMemsetAsync(v.changed, 0, 2 * sizeof(uint32_t), L.stream);
     k_static_sweep<<<L.fit(k_static_sweep, SW_WARPS * 32, 0), SW_WARPS * 32, 0, L.stream>>>(w, v);
     L.mark("k_static_sweep");
 }
@@ -345,12 +533,5 @@ void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, c
     L.mark("k_pixel_latest");
 }
 
-void launch_global_round(const Work &w, const VarWork &v, const Launch &L) {
-    cudaMemsetAsync(v.changed, 0, sizeof(uint32_t), L.stream);
-    k_group_last_reset<<<L.fit(k_group_last_reset, 256, 0), 256, 0, L.stream>>>(w, v);
-    k_group_last<<<L.fit(k_group_last, 256, 0), 256, 0, L.stream>>>(w, v);
-    k_global_round<<<L.fit(k_global_round, 256, 0), 256, 0, L.stream>>>(w, v);
-    L.mark("k_global_round");
-}
 
 }  // namespace tpc

@@ -137,3 +137,13 @@ def test_issue_roofline_from_stored_instruction_count(tmp_path, monkeypatch):
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert bench.issue_roofline("k_tile_link_table", 2**26, 2.0, 152, None) is None
     assert bench.issue_roofline("k_accumulate", 2**26, 2.0, 152, 2000.0) is None
+
+
+def test_forest_depth_of_a_hand_built_forest():
+    """Steps to the root of every node (the union-find depth metric)."""
+    import numpy as np
+    import bench
+    # 0 <- 1 <- 2 <- 3, 2 <- 4; 5 <- 6
+    d = bench.forest_depth(np.array([0, 0, 1, 2, 2, 5, 5], dtype=np.uint32))
+    assert d == {"max": 3, "mean": pytest.approx(10 / 7), "nodes": 7, "roots": 2, "deeper_than_1": 3}
+    assert bench.forest_depth(np.arange(5, dtype=np.uint32))["max"] == 0

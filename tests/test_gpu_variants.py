@@ -74,3 +74,41 @@ def test_refinement_on_device():
     ai, bi, ci = (x.astype(np.int64) for x in (a, b, c))
     assert np.all(a == a[ci])      # (c) refines (a)
     assert np.all(b == b[ai])      # (a) refines (b)
+
+
+def _gpu_stats(hits, w, h, dt, variant):
+    from paper_2412_11809_gb300 import Clusterer
+    with Clusterer(w, h, dt, variant) as c:
+        c.push(hits)
+        c.flush()
+        lab = c.labels()
+        st = c.variant_stats()
+    np.testing.assert_array_equal(lab, oracle.labels(hits, w, h, dt, variant))
+    return st
+
+
+def test_device_paths_are_reached():
+    """The paths the large workloads take, each against the oracle: (c)
+    components longer than the shared-memory staging swept through the
+    sliding window, and swept again from global memory when more hits than
+    the window holds lie within dt; (b) several rounds over the open-edge
+    list, with an exact recomputation of the groups' last ToA at the end, and
+    full passes when that list overflows."""
+    hits, _ = synth.cfg4(scale=1 / 128, seed=25)          # 4 Mi hits at 2.5 Ghits/s density
+    st = _gpu_stats(hits, 448, 512, 128, "static")
+    assert st["windowed"] > 0 and st["window_fallbacks"] == 0, st
+    st = _gpu_stats(hits, 448, 512, 128, "global")
+    assert st["rounds"] >= 3 and st["exact_checks"] >= 1, st
+    rng = np.random.default_rng(31)
+    same = random_hits(rng, 8000, 60, 40, 0)               # one ToA: every hit within dt of every other
+    st = _gpu_stats(same, 60, 40, 0, "static")
+    assert st["windowed"] > 0 and st["window_fallbacks"] == st["windowed"], st
+    # sparse hits, most of whose latest neighbours lie in closed groups (more
+    # open edges than the list holds), around one pixel firing every 2 ticks:
+    # its group stays open and takes in its neighbourhood round by round
+    bg = random_hits(rng, 16000, 40, 40, 50000)
+    fire = oracle.make_hits(np.full(25000, 20), np.full(25000, 20), np.arange(25000) * 2).astype(bg.dtype)
+    mix = np.concatenate([bg, fire])
+    mix = mix[np.argsort(mix["toa"], kind="stable")]
+    st = _gpu_stats(mix, 40, 40, 3, "global")
+    assert st["full_rounds"] >= 2 and st["rounds"] >= 2, st   # the open-edge list overflowed

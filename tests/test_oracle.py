@@ -234,3 +234,25 @@ def test_out_of_range_rejected():
     bad = oracle.make_hits([4], [0], [0])
     with pytest.raises(ValueError):
         oracle.labels(bad, 4, 4, 10)
+
+
+def test_concurrent_calls_agree_with_sequential():
+    """The oracle is called from several threads at once by the full-size
+    tests (the C library releases the GIL): each thread's result must equal
+    the same call made alone."""
+    import threading
+    streams = [synth.cfg1(scale=1 / 512, seed=900 + k)[0] for k in range(4)]
+    want = [oracle.labels(h, 256, 256, 128, v) for h, v in zip(streams, ("local", "global", "static", "local"))]
+    got = [None] * 4
+
+    def run(k, v):
+        got[k] = oracle.labels(streams[k], 256, 256, 128, v)
+
+    threads = [threading.Thread(target=run, args=(k, v))
+               for k, v in enumerate(("local", "global", "static", "local"))]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    for g, w in zip(got, want):
+        np.testing.assert_array_equal(g, w)
