@@ -357,8 +357,6 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
 // reset afterwards (Algorithm 3 step 7).
 constexpr int TAB_THREADS = 1024;
 constexpr uint16_t TAB_NONE = 0xFFFFu;
-constexpr uint16_t TAB_MORE = 0x1000u;   // head entry flag: its list holds a second hit
-constexpr uint16_t TAB_RANK = 0x0FFFu;   // head entry: rank of the list's first hit
 constexpr int TAB_WALK = 64;
 constexpr int TAB_EDGES = 3 * TILE / 2;
 constexpr int CAND = 6;
@@ -382,21 +380,15 @@ __device__ __forceinline__ uint32_t tab_pid(uint32_t pix, uint32_t W) {
     return ((pix >> 16) + 1) * (W + 2) + (pix & 0xFFFFu) + 1;
 }
 
-// push rank k on pixel pid's list; returns the rank of the previous head
-// (TAB_NONE if the list was empty).  The head entry carries TAB_MORE when
-// the list then holds more than one hit, so that the walk reads a list's
-// second entry only where there is one.
+// push rank k on pixel pid's list; returns the previous head
 __device__ __forceinline__ uint16_t tab_push(uint16_t *tab, uint32_t pid, uint16_t k) {
-    static_assert(TILE - 1 <= TAB_RANK, "ranks fit the head entry");
     uint32_t *word = reinterpret_cast<uint32_t *>(tab) + (pid >> 1);
     const uint32_t shift = (pid & 1u) * 16u;
     uint32_t old = *reinterpret_cast<volatile uint32_t *>(word);
     while (true) {
-        const uint32_t prev = (old >> shift) & 0xFFFFu;
-        const uint32_t entry = prev == TAB_NONE ? k : (k | TAB_MORE);
-        const uint32_t nv = (old & ~(0xFFFFu << shift)) | (entry << shift);
+        const uint32_t nv = (old & ~(0xFFFFu << shift)) | ((uint32_t)k << shift);
         const uint32_t seen = atomicCAS(word, old, nv);
-        if (seen == old) return prev == TAB_NONE ? TAB_NONE : (uint16_t)(prev & TAB_RANK);
+        if (seen == old) return (uint16_t)(old >> shift);
         old = seen;
     }
 }
@@ -460,16 +452,17 @@ __device__ __forceinline__ void tab_walk(TabShared &S, uint32_t k, uint32_t key,
     uint32_t more = 0;
 #pragma unroll
     for (int n = 0; n < 9; ++n) {
-        const bool has = hd[n] != TAB_NONE;
-        const uint32_t j = hd[n] & TAB_RANK;
-        const uint32_t kj = has ? S.key[j] : 0u;
-        more |= (has && (hd[n] & TAB_MORE) ? 1u : 0u) << n;
+        const uint32_t j = hd[n];
+        const uint32_t jm = j & (TILE - 1);   // an empty head reads a harmless entry
+        const uint32_t kj = S.key[jm], nx = S.next[jm];
+        const bool has = j != TAB_NONE;
+        more |= (has && nx != TAB_NONE ? 1u : 0u) << n;
         if (has && j < k && key - kj <= dt) consider(j);
     }
     while (more) {   // lists holding more than one hit
         const int n = __ffs(more) - 1;
         more &= more - 1;
-        uint32_t j = S.next[hd[n] & TAB_RANK];
+        uint32_t j = S.next[hd[n]];
         int steps = 1;
         for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps)
             if (j < k && key - S.key[j] <= dt) consider(j);

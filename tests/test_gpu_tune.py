@@ -26,11 +26,15 @@ def _batch(scale, seed):
     return dets, ctxs, d_hits
 
 
-def _check(dets, ctxs):
+def _check(dets, ctxs, base=0):
+    """Labels are global stream indices: after `base` earlier hits per
+    detector, the oracle's labels shifted by base."""
     for c, (w, h, hits, _, _) in zip(ctxs, dets):
         want = oracle.labels(hits, w, h, 128)
-        np.testing.assert_array_equal(c.labels(), want)
-        assert_features_equal(c.features(), oracle.features(hits, want))
+        np.testing.assert_array_equal(c.labels() - np.uint64(base * len(hits)), want)
+        rec = c.features()
+        rec["label"] -= np.uint64(base * len(hits))
+        assert_features_equal(rec, oracle.features(hits, want))
 
 
 @pytest.mark.parametrize("choice", [
@@ -74,7 +78,7 @@ def test_tuner_chooses_caches_and_keeps_results(tmp_path):
     assert rep2.chosen.as_dict() == rep.chosen.as_dict()
     assert ctxs[0].tuning().as_dict() == rep.chosen.as_dict()
     batch_flush(ctxs)
-    _check(dets, ctxs)
+    _check(dets, ctxs, base=1)   # each detector's stream went on after its first batch
     for c in ctxs:
         c.close()
 

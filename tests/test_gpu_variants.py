@@ -103,12 +103,15 @@ def test_device_paths_are_reached():
     same = random_hits(rng, 8000, 60, 40, 0)               # one ToA: every hit within dt of every other
     st = _gpu_stats(same, 60, 40, 0, "static")
     assert st["windowed"] > 0 and st["window_fallbacks"] == st["windowed"], st
-    # sparse hits, most of whose latest neighbours lie in closed groups (more
-    # open edges than the list holds), around one pixel firing every 2 ticks:
-    # its group stays open and takes in its neighbourhood round by round
-    bg = random_hits(rng, 16000, 40, 40, 50000)
-    fire = oracle.make_hits(np.full(25000, 20), np.full(25000, 20), np.arange(25000) * 2).astype(bg.dtype)
-    mix = np.concatenate([bg, fire])
+    # every pixel of a 30 x 30 sensor fires 20 times at random, far apart in
+    # time: almost every hit's 9 latest neighbours lie in other, closed groups,
+    # more open edges than the list holds; plus one merge that only (b) makes
+    # (h joins L's group through its member M, which h is not adjacent to)
+    t = rng.integers(0, 10**7, size=(900, 20))
+    px = np.repeat(np.arange(900), 20)
+    bg = oracle.make_hits(px % 30, px // 30, t.ravel())
+    lmh = oracle.make_hits([10, 11, 9], [10, 11, 10], [20_000_000, 20_000_003, 20_000_005])  # L, M, h
+    mix = np.concatenate([bg, lmh.astype(bg.dtype)])
     mix = mix[np.argsort(mix["toa"], kind="stable")]
-    st = _gpu_stats(mix, 40, 40, 3, "global")
+    st = _gpu_stats(mix, 30, 30, 3, "global")
     assert st["full_rounds"] >= 2 and st["rounds"] >= 2, st   # the open-edge list overflowed
