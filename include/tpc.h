@@ -258,12 +258,13 @@ int tpc_forest(tpc_ctx *ctx, uint32_t *parent, uint32_t *input_pos, size_t cap, 
    otherwise): (b) rounds of merges on the device, of which full passes over
    every hit (the first, and any after the list of open edges overflowed),
    and exact recomputations of the groups' last ToA; (c) components longer
-   than the shared-memory staging, swept through its sliding window, and of
-   those the ones swept again from global memory (more hits within dt than
-   the window holds).  Waits for the context's work. */
+   than the shared-memory staging, swept through a sliding window of 512
+   hits; of those, the ones swept again through a window of 8192 hits (more
+   hits within dt than the first window holds), and of those the ones swept
+   from global memory.  Waits for the context's work. */
 typedef struct tpc_variant_stats {
     uint32_t rounds, full_rounds, exact_checks;
-    uint32_t windowed, window_fallbacks;
+    uint32_t windowed, window_fallbacks, global_sweeps;
 } tpc_variant_stats;
 int tpc_variant_stats_get(tpc_ctx *ctx, tpc_variant_stats *out);
 

@@ -875,6 +875,7 @@ cudaError_t init_kernel_attributes() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_tile_link_table, cudaFuncAttributeMaxDynamicSharedMemorySize, TAB_SMEM);
     if (e == cudaSuccess) e = init_features_attributes();
+    if (e == cudaSuccess) e = init_variants_attributes();
     return e == cudaSuccess ? init_sortfast_attributes() : e;
 }
 

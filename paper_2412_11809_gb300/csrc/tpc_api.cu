@@ -230,6 +230,7 @@ struct VarSpace {
         v.glast = mem.alloc<uint32_t>(positions, e);
         v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
         v.latest = mem.alloc<uint32_t>(9 * positions, e);
+        v.lat_stride = (uint32_t)positions;
         v.changed = mem.alloc<uint32_t>(4, e);
         // open (b) edges: 4 per position per list; a round that finds more
         // marks the overflow and the next round reads every hit's 9 again
@@ -237,6 +238,7 @@ struct VarSpace {
         v.edges[0] = mem.alloc<uint2>(v.edge_cap, e);
         v.edges[1] = mem.alloc<uint2>(v.edge_cap, e);
         v.work = mem.alloc<uint32_t>(1, e);
+        v.big = mem.alloc<uint2>(positions / 512 + 1, e);   // components of more than 512 hits
         v.prob = mem.alloc<Prob>(1, e);
         if (e != cudaSuccess) {
             mem.release();
@@ -812,7 +814,7 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
         for (int pass = 0; pass < 4; ++pass) launch_radix_pass(wv, pass, L);
         launch_static_sweep(w, v, L);
         c->vstats = tpc_variant_stats{};
-        if (cudaMemcpyAsync(c->h_flag, v.changed, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
+        if (cudaMemcpyAsync(c->h_flag, v.changed, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess)
             return TPC_ERR_CUDA;
         c->vstats_pending = true;   // read at tpc_variant_stats, after the stream
@@ -1192,6 +1194,7 @@ int tpc_variant_stats_get(tpc_ctx *c, tpc_variant_stats *out) {
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPC_ERR_CUDA;
         c->vstats.windowed = c->h_flag[0];
         c->vstats.window_fallbacks = c->h_flag[1];
+        c->vstats.global_sweeps = c->h_flag[2];
         c->vstats_pending = false;
     }
     *out = c->vstats;

@@ -142,12 +142,15 @@ struct VarWork {
     uint32_t *cpar;            // (c): forest over the root-grouped order
     uint32_t *glast;           // (b): per root, last key of its group
     uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
-    uint32_t *latest;          // (b): per position, 9 slots: latest earlier hit on each neighbour pixel
+    uint32_t *latest;          // (b): [9][lat_stride]: for the hit at each pixel-timeline index, the
+                               //      latest earlier hit (sorted position) on each neighbour pixel
+    uint32_t lat_stride;       // (b): entries per direction of latest
     uint32_t *changed;         // (b): [0] a round merged something, [1] the edge list overflowed,
                                //      [2], [3] entries in edge lists 0 and 1
     uint2 *edges[2];           // (b): edges (hit, latest neighbour) not merged yet, ping-pong
     uint32_t edge_cap;         // (b): entries each edge list holds
     uint32_t *work;            // (c): next chunk of the grouped order to sweep
+    uint2 *big;                // (c): (first grouped position, hits) of components for the big window
     Prob *prob;                // problem view of the grouping sort
 };
 
@@ -326,6 +329,7 @@ struct Launch {
 };
 
 cudaError_t init_kernel_attributes();   // once per process and device, before capture
+cudaError_t init_variants_attributes();
 void launch_setup(const Work &w, int nsegs, const Launch &L);
 void launch_seg_finalize(const Work &w, const Launch &L);
 void launch_make_keys(const Work &w, const Launch &L);

@@ -141,50 +141,55 @@ __device__ void sweep_component(const SweepView<STAGED> &V, uint32_t n, uint32_t
 // leaving, its root goes to global memory (cpar, by component index, and
 // the parent array); finds that reach a hit that has left read it there.  A
 // batch of 32 hits enters every 32 steps, pushing the 32 oldest out; if one
-// of those is within dt of the first newcomer, the window is too small and
-// the component is swept again from global memory (returns false).
+// of those is within dt of the first newcomer, the window is too small
+// (returns false): the component is listed for k_static_sweep_big, which
+// sweeps it again through a window of BIG_CAP hits (one warp per CTA, the
+// window in dynamic shared memory), or, should that overflow too, from
+// global memory.
+template <uint32_t CAP>
 struct WindowView {
     uint32_t *wk, *wp, *wc;    // window: key, pixel, parent (component index)
     uint32_t *cpar;            // global: final root of each hit that left
     uint32_t lo;               // first component index still in the window
-    __device__ uint32_t key(uint32_t i) const { return wk[i % SW_CAP]; }
-    __device__ uint32_t pix(uint32_t i) const { return wp[i % SW_CAP]; }
+    __device__ uint32_t key(uint32_t i) const { return wk[i % CAP]; }
+    __device__ uint32_t pix(uint32_t i) const { return wp[i % CAP]; }
     __device__ uint32_t find(uint32_t x) const {
         volatile uint32_t *c = wc;
         while (true) {
             if (x < lo) return *reinterpret_cast<volatile uint32_t *>(&cpar[x]);
-            const uint32_t p = c[x % SW_CAP];
+            const uint32_t p = c[x % CAP];
             if (p == x) return x;
             if (p < lo) return *reinterpret_cast<volatile uint32_t *>(&cpar[p]);
-            const uint32_t gp = c[p % SW_CAP];
+            const uint32_t gp = c[p % CAP];
             if (gp == p) return p;
-            c[x % SW_CAP] = gp;
+            c[x % CAP] = gp;
             x = gp;
         }
     }
 };
 
-__device__ bool sweep_windowed(WindowView V, const uint32_t *skey, const uint32_t *spix, const uint32_t *gv,
+template <uint32_t CAP>
+__device__ bool sweep_windowed(WindowView<CAP> V, const uint32_t *skey, const uint32_t *spix, const uint32_t *gv,
                                uint32_t *parent, uint32_t q0, uint32_t n, uint32_t dt, int lane) {
     for (uint32_t i = 0; i < n; ++i) {
-        if ((i & 31u) == 0) {   // hits [i, i + 32) enter, [i - SW_CAP, i - SW_CAP + 32) leave
+        if ((i & 31u) == 0) {   // hits [i, i + 32) enter, [i - CAP, i - CAP + 32) leave
             const uint32_t ki = skey[gv[q0 + i]];
-            if (i >= SW_CAP) {
-                const uint32_t j = i - SW_CAP + lane;   // < i <= n - 1
+            if (i >= CAP) {
+                const uint32_t j = i - CAP + lane;   // < i <= n - 1
                 if (__any_sync(0xffffffffu, ki - V.key(j) <= dt)) return false;
                 const uint32_t r = V.find(j);
                 __syncwarp();
                 V.cpar[j] = r;
                 parent[gv[q0 + j]] = gv[q0 + r];
                 __syncwarp();
-                V.lo = i - SW_CAP + 32;
+                V.lo = i - CAP + 32;
             }
             const uint32_t e = i + lane;
             if (e < n) {
                 const uint32_t se = gv[q0 + e];
-                V.wk[e % SW_CAP] = skey[se];
-                V.wp[e % SW_CAP] = spix[se];
-                V.wc[e % SW_CAP] = e;
+                V.wk[e % CAP] = skey[se];
+                V.wp[e % CAP] = spix[se];
+                V.wc[e % CAP] = e;
             }
             __syncwarp();
         }
@@ -205,13 +210,13 @@ __device__ bool sweep_windowed(WindowView V, const uint32_t *skey, const uint32_
             __syncwarp();
             if (m != 0xFFFFFFFFu) {
                 const uint32_t target = m < root ? m : root;
-                if (r != 0xFFFFFFFFu && r != target) V.wc[r % SW_CAP] = target;
-                if (lane == 0 && root != 0xFFFFFFFFu && root != target) V.wc[root % SW_CAP] = target;
+                if (r != 0xFFFFFFFFu && r != target) V.wc[r % CAP] = target;
+                if (lane == 0 && root != 0xFFFFFFFFu && root != target) V.wc[root % CAP] = target;
                 root = target;
             }
             __syncwarp();
         }
-        if (lane == 0 && root != 0xFFFFFFFFu) V.wc[i % SW_CAP] = root;
+        if (lane == 0 && root != 0xFFFFFFFFu) V.wc[i % CAP] = root;
         __syncwarp();
     }
     // the hits still in the window
@@ -266,19 +271,51 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_static_sweep(Work w, VarWork 
                 sweep_component(V, n, dt, lane);
                 for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
             } else {
-                const WindowView WV{s_k[warp], s_p[warp], s_c[warp], v.cpar + q0, 0};
+                const WindowView<SW_CAP> WV{s_k[warp], s_p[warp], s_c[warp], v.cpar + q0, 0};
                 if (lane == 0) atomicAdd(&v.changed[0], 1u);   // diagnostics: windowed components
                 if (!sweep_windowed(WV, skey, w.spix, gv, w.parent, q0, n, dt, lane)) {
-                    if (lane == 0) atomicAdd(&v.changed[1], 1u);   // ... and those swept again
-                    __syncwarp();   // more than the window within dt: from global memory
-                    const SweepView<false> V{nullptr, nullptr, v.cpar + q0, skey, w.spix, gv, q0};
-                    sweep_component(V, n, dt, lane);
-                    for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
+                    if (lane == 0) {   // more than the window within dt: the big window's list
+                        const uint32_t k = atomicAdd(&v.changed[1], 1u);
+                        v.big[k] = make_uint2(q0, n);   // k < positions / SW_CAP: each has > SW_CAP hits
+                    }
+                    __syncwarp();
                 }
             }
             __syncwarp();   // the staging is rewritten for the next component
         }
     }
+}
+
+// (c): components whose hits within dt outgrew the warp's window, one warp
+// per CTA through a window of BIG_CAP hits in dynamic shared memory; from
+// global memory if even that overflows.
+constexpr uint32_t BIG_CAP = 8192;
+constexpr int BIG_SMEM = 3 * BIG_CAP * (int)sizeof(uint32_t);
+
+__global__ void __launch_bounds__(32) k_static_sweep_big(Work w, VarWork v) {
+    extern __shared__ uint32_t big_raw[];
+    const Prob &P = *w.prob;
+    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *gv = v.v[v.prob->npasses & 1u];
+    const uint32_t dt = w.seg[0].dt, nbig = v.changed[1];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t k = blockIdx.x; k < nbig; k += gridDim.x) {
+        const uint2 job = v.big[k];
+        const uint32_t q0 = job.x, n = job.y;
+        const WindowView<BIG_CAP> WV{big_raw, big_raw + BIG_CAP, big_raw + 2 * BIG_CAP, v.cpar + q0, 0};
+        if (!sweep_windowed(WV, skey, w.spix, gv, w.parent, q0, n, dt, lane)) {
+            if (lane == 0) atomicAdd(&v.changed[2], 1u);   // diagnostics: swept from global memory
+            __syncwarp();
+            const SweepView<false> V{nullptr, nullptr, v.cpar + q0, skey, w.spix, gv, q0};
+            sweep_component(V, n, dt, lane);
+            for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t init_variants_attributes() {
+    return cudaFuncSetAttribute(k_static_sweep_big, cudaFuncAttributeMaxDynamicSharedMemorySize, BIG_SMEM);
 }
 
 // (b): pixel histogram and its exclusive scan (single segment).
@@ -321,35 +358,44 @@ __global__ void __launch_bounds__(1024) k_pixel_scan(Work w, VarWork v) {
 }
 
 // (b), once before the rounds: for every hit and each of its 9 pixels the
-// latest earlier hit there (binary search in the pixel's timeline), or none.
+// latest earlier hit there, or none.  One thread per (pixel p, direction):
+// p's timeline and its neighbour q's are both in (ToA, position) order, so
+// one forward pass with a pointer into q's timeline finds, for each hit of
+// p, the last hit of q before it (the same pixel: the previous entry).  The
+// results are stored in timeline order, latest[d * stride + i] for the hit
+// at timeline index i, so each thread writes a contiguous run.
 __global__ void __launch_bounds__(256) k_pixel_latest(Work w, VarWork v) {
-    const Prob &P = *w.prob;
-    const uint32_t nt = P.ntiles;
-    const uint32_t *tl = v.v[v.prob->npasses & 1u];   // sorted positions grouped by pixel
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-        const Seg &g = w.seg[w.tile_seg[t]];
-        uint32_t begin, end;
-        tile_range(g, t, begin, end);
-        const uint32_t W = g.width, H = g.height;
-        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
-            const uint32_t pix = w.spix[s];
-            const int x = (int)(pix & 0xFFFFu), y = (int)(pix >> 16);
-#pragma unroll
-            for (int n = 0; n < 9; ++n) {
-                const int nx = x + n % 3 - 1, ny = y + n / 3 - 1;
-                uint32_t L = 0xFFFFFFFFu;
-                if (nx >= 0 && nx < (int)W && ny >= 0 && ny < (int)H) {
-                    const uint32_t p = (uint32_t)ny * W + (uint32_t)nx;
-                    const uint32_t first = v.pix_start[p];
-                    uint32_t lo = first, hi = v.pix_start[p + 1];   // last entry < s
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (tl[g.off + mid] < s) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo != first) L = tl[g.off + lo - 1];
-                }
-                v.latest[(size_t)s * 9 + n] = L;
+    const Seg &g = w.seg[0];
+    const uint32_t W = g.width, H = g.height, np = W * H;
+    const uint32_t *tl = v.v[v.prob->npasses & 1u] + g.off;   // sorted positions grouped by pixel
+    const uint32_t tasks = 9u * np;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
+        const uint32_t d = t / np, p = t - d * np;
+        const uint32_t p0 = v.pix_start[p], p1 = v.pix_start[p + 1];
+        if (p0 == p1) continue;
+        uint32_t *out = v.latest + (size_t)d * v.lat_stride;
+        const int x = (int)(p % W) + (int)(d % 3) - 1, y = (int)(p / W) + (int)(d / 3) - 1;
+        if (x < 0 || x >= (int)W || y < 0 || y >= (int)H) {
+            for (uint32_t i = p0; i < p1; ++i) out[i] = 0xFFFFFFFFu;
+            continue;
+        }
+        if (d == 4) {   // the pixel itself: the previous hit of the timeline
+            out[p0] = 0xFFFFFFFFu;
+            for (uint32_t i = p0 + 1; i < p1; ++i) out[i] = tl[i - 1];
+            continue;
+        }
+        const uint32_t q = (uint32_t)y * W + (uint32_t)x;
+        const uint32_t q0 = v.pix_start[q], q1 = v.pix_start[q + 1];
+        uint32_t j = q0, last = 0xFFFFFFFFu;
+        for (uint32_t i = p0; i < p1; ++i) {
+            const uint32_t s = tl[i];
+            while (j < q1) {
+                const uint32_t c = tl[j];
+                if (c >= s) break;
+                last = c;
+                ++j;
             }
+            out[i] = last;
         }
     }
 }
@@ -402,16 +448,20 @@ __device__ __forceinline__ void gunion_last(uint32_t *parent, uint32_t *glast, u
     }
 }
 
-// Apply the rule to one edge (hit s, latest earlier hit l on one of its 9
-// pixels); returns 1 if merged, 0 if the groups already agree, 2 if the
-// edge stays open (its groups differ and the rule does not hold yet).
-__device__ __forceinline__ int global_edge(const Work &w, const VarWork &v, const uint32_t *skey, uint32_t dt,
-                                           uint32_t s, uint32_t l) {
-    const uint32_t rl = gfind(w.parent, l), rh = gfind(w.parent, s);
+// Apply the rule to one edge (hit s with key ks and current root rh, latest
+// earlier hit l on one of its 9 pixels); returns 1 if merged (rh then holds
+// s's new root), 0 if the groups already agree, 2 if the edge stays open
+// (its groups differ and the rule does not hold yet).
+__device__ __forceinline__ int global_edge(const Work &w, const VarWork &v, uint32_t ks, uint32_t dt, uint32_t s,
+                                           uint32_t &rh, uint32_t l) {
+    const uint32_t rl = gfind(w.parent, l);
+    if (rl == rh) return 0;
+    rh = gfind(w.parent, rh);   // a concurrent union may have moved s's root
     if (rl == rh) return 0;
     const uint32_t last = *reinterpret_cast<volatile uint32_t *>(&v.glast[rl]);
-    if ((uint64_t)skey[s] <= (uint64_t)last + dt) {
+    if ((uint64_t)ks <= (uint64_t)last + dt) {
         gunion_last(w.parent, v.glast, s, l);
+        rh = gfind(w.parent, s);
         return 1;
     }
     return 2;
@@ -434,28 +484,27 @@ __device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep,
 }
 
 // A round over every hit's 9 latest neighbours (the first round, and any
-// round after an overflow): merges what the rule allows, lists the rest.
+// round after an overflow), in pixel-timeline order: merges what the rule
+// allows, lists the rest.
 __global__ void __launch_bounds__(256) k_global_full(Work w, VarWork v, int out) {
     const Prob &P = *w.prob;
-    const uint32_t nt = P.ntiles;
+    const Seg &g = w.seg[0];
     const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *tl = v.v[v.prob->npasses & 1u] + g.off;
+    const uint32_t n = g.n, dt = g.dt;
     bool changed = false;
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-        const Seg &g = w.seg[w.tile_seg[t]];
-        uint32_t begin, end;
-        tile_range(g, t, begin, end);
-        const uint32_t dt = g.dt;
-        for (uint32_t s0 = begin; s0 < end; s0 += blockDim.x) {   // whole warps: the ballots below
-            const uint32_t s = s0 + threadIdx.x;
-            const bool valid = s < end;
+    for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {   // whole warps: ballots
+        const uint32_t i = i0 + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t s = valid ? tl[i] : 0, ks = valid ? skey[s] : 0;
+        uint32_t rh = valid ? gfind(w.parent, s) : 0;
 #pragma unroll 1
-            for (int n = 0; n < 9; ++n) {
-                const uint32_t l = valid ? v.latest[(size_t)s * 9 + n] : 0xFFFFFFFFu;
-                int r = 0;
-                if (l != 0xFFFFFFFFu) r = global_edge(w, v, skey, dt, s, l);
-                changed |= r == 1;
-                push_edges(v, out, r == 2, s, l);
-            }
+        for (int d = 0; d < 9; ++d) {
+            const uint32_t l = valid ? v.latest[(size_t)d * v.lat_stride + i] : 0xFFFFFFFFu;
+            int r = 0;
+            if (l != 0xFFFFFFFFu) r = global_edge(w, v, ks, dt, s, rh, l);
+            changed |= r == 1;
+            push_edges(v, out, r == 2, s, l);
         }
     }
     if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&v.changed[0], 1u);
@@ -474,7 +523,11 @@ __global__ void __launch_bounds__(256) k_global_list(Work w, VarWork v, int in) 
         const uint32_t e = e0 + threadIdx.x;
         const bool valid = e < cnt;
         const uint2 ed = valid ? v.edges[in][e] : make_uint2(0, 0);
-        const int r = valid ? global_edge(w, v, skey, dt, ed.x, ed.y) : 0;
+        int r = 0;
+        if (valid) {
+            uint32_t rh = gfind(w.parent, ed.x);
+            r = global_edge(w, v, skey[ed.x], dt, ed.x, rh, ed.y);
+        }
         changed |= r == 1;
         push_edges(v, 1 - in, r == 2, ed.x, ed.y);
     }
@@ -519,9 +572,11 @@ Work variant_view(const Work &w, const VarWork &v) {
 
 void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L) {
     cudaMemsetAsync(v.work, 0, sizeof(uint32_t), L.stream);
-    cudaMemsetAsync(v.changed, 0, 2 * sizeof(uint32_t), L.stream);
+    cudaMemsetAsync(v.changed, 0, 3 * sizeof(uint32_t), L.stream);
     k_static_sweep<<<L.fit(k_static_sweep, SW_WARPS * 32, 0), SW_WARPS * 32, 0, L.stream>>>(w, v);
     L.mark("k_static_sweep");
+    k_static_sweep_big<<<L.fit(k_static_sweep_big, 32, BIG_SMEM), 32, BIG_SMEM, L.stream>>>(w, v);
+    L.mark("k_static_sweep_big");
 }
 
 void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, const Launch &L) {
