@@ -258,10 +258,11 @@ int tpc_forest(tpc_ctx *ctx, uint32_t *parent, uint32_t *input_pos, size_t cap, 
    otherwise): (b) rounds of merges on the device, of which full passes over
    every hit (the first, and any after the list of open edges overflowed),
    and exact recomputations of the groups' last ToA; (c) components longer
-   than the shared-memory staging, swept through a sliding window of 512
-   hits; of those, the ones swept again through a window of 8192 hits (more
-   hits within dt than the first window holds), and of those the ones swept
-   from global memory.  Waits for the context's work. */
+   than a warp's shared-memory staging (512 hits), swept by one warp
+   through a sliding window of 512 hits; of those, the ones swept again by a
+   whole CTA (more hits within dt than that window holds), and of those the
+   ones too long (over 8192 hits) to stage in shared memory, swept from
+   global memory.  Waits for the context's work. */
 typedef struct tpc_variant_stats {
     uint32_t rounds, full_rounds, exact_checks;
     uint32_t windowed, window_fallbacks, global_sweeps;

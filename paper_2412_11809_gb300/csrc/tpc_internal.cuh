@@ -139,7 +139,7 @@ struct Work {
 // Extra arrays of the (b)/(c) variants (single-segment steps only).
 struct VarWork {
     uint32_t *k[2], *v[2];     // grouping radix sort: keys / sorted positions
-    uint32_t *cpar;            // (c): forest over the root-grouped order
+    uint32_t *cpar;            // (c): forest over the root-grouped order; (b): timeline index of each position
     uint32_t *glast;           // (b): per root, last key of its group
     uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
     uint32_t *latest;          // (b): [9][lat_stride]: for the hit at each pixel-timeline index, the

@@ -143,9 +143,8 @@ __device__ void sweep_component(const SweepView<STAGED> &V, uint32_t n, uint32_t
 // batch of 32 hits enters every 32 steps, pushing the 32 oldest out; if one
 // of those is within dt of the first newcomer, the window is too small
 // (returns false): the component is listed for k_static_sweep_big, which
-// sweeps it again through a window of BIG_CAP hits (one warp per CTA, the
-// window in dynamic shared memory), or, should that overflow too, from
-// global memory.
+// sweeps it again with a whole CTA, staged in shared memory up to BIG_CAP
+// hits, from global memory beyond.
 template <uint32_t CAP>
 struct WindowView {
     uint32_t *wk, *wp, *wc;    // window: key, pixel, parent (component index)
@@ -286,31 +285,81 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_static_sweep(Work w, VarWork 
     }
 }
 
-// (c): components whose hits within dt outgrew the warp's window, one warp
-// per CTA through a window of BIG_CAP hits in dynamic shared memory; from
-// global memory if even that overflows.
+// (c): components whose hits within dt outgrew the warp's window.  One CTA
+// per component, the component staged whole in dynamic shared memory (up to
+// BIG_CAP hits; from global memory beyond): the same sweep, with each
+// step's candidates (the earlier hits within dt) spread over the CTA's
+// threads instead of one warp's lanes, the earliest open root found by a
+// shared-memory minimum.
+constexpr int BIG_THREADS = 512;
 constexpr uint32_t BIG_CAP = 8192;
 constexpr int BIG_SMEM = 3 * BIG_CAP * (int)sizeof(uint32_t);
 
-__global__ void __launch_bounds__(32) k_static_sweep_big(Work w, VarWork v) {
+template <bool STAGED>
+__device__ void sweep_block(const SweepView<STAGED> &V, uint32_t n, uint32_t dt, uint32_t *s_min) {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) V.sc[i] = i;
+    if (threadIdx.x < 2) s_min[threadIdx.x] = 0xFFFFFFFFu;
+    __syncthreads();
+    uint32_t it = 0;   // iterations so far: s_min[it & 1] collects this one's minimum
+    for (uint32_t i = 1; i < n; ++i) {
+        const uint32_t ki = V.key(i), pi = V.pix(i);
+        uint32_t root = 0xFFFFFFFFu;   // the earliest open root joined so far (the same in every thread)
+        for (uint32_t base = 0; base < i; base += blockDim.x, ++it) {
+            const bool valid = base + threadIdx.x < i;
+            const uint32_t j = valid ? i - 1 - base - threadIdx.x : 0;
+            const bool in = valid && ki - V.key(j) <= dt;
+            uint32_t r = 0xFFFFFFFFu;
+            if (in && adjacent_v(pi, V.pix(j))) {
+                const uint32_t rj = V.find(j);
+                if (ki - V.key(rj) <= dt) r = rj;   // that cluster is still open
+            }
+            uint32_t *mn = s_min + (it & 1u);
+            if (r != 0xFFFFFFFFu) atomicMin(mn, r);
+            const bool any_in = __syncthreads_or(in);
+            const uint32_t m = *reinterpret_cast<volatile uint32_t *>(mn);
+            if (threadIdx.x == 0) s_min[(it + 1) & 1u] = 0xFFFFFFFFu;   // read by nobody until the next barrier
+            if (m != 0xFFFFFFFFu) {
+                const uint32_t target = m < root ? m : root;
+                if (r != 0xFFFFFFFFu && r != target) V.sc[r] = target;
+                if (threadIdx.x == 0 && root != 0xFFFFFFFFu && root != target) V.sc[root] = target;
+                root = target;
+            }
+            __syncthreads();
+            if (!any_in) { ++it; break; }   // keys only fall further back
+        }
+        if (threadIdx.x == 0 && root != 0xFFFFFFFFu) V.sc[i] = root;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(BIG_THREADS) k_static_sweep_big(Work w, VarWork v) {
     extern __shared__ uint32_t big_raw[];
+    __shared__ uint32_t s_min[2];
     const Prob &P = *w.prob;
     const uint32_t *skey = w.keys[sorted_sel(P)];
     const uint32_t *gv = v.v[v.prob->npasses & 1u];
     const uint32_t dt = w.seg[0].dt, nbig = v.changed[1];
-    const int lane = threadIdx.x & 31;
     for (uint32_t k = blockIdx.x; k < nbig; k += gridDim.x) {
         const uint2 job = v.big[k];
         const uint32_t q0 = job.x, n = job.y;
-        const WindowView<BIG_CAP> WV{big_raw, big_raw + BIG_CAP, big_raw + 2 * BIG_CAP, v.cpar + q0, 0};
-        if (!sweep_windowed(WV, skey, w.spix, gv, w.parent, q0, n, dt, lane)) {
-            if (lane == 0) atomicAdd(&v.changed[2], 1u);   // diagnostics: swept from global memory
-            __syncwarp();
+        if (n <= BIG_CAP) {
+            uint32_t *sk = big_raw, *sp = big_raw + BIG_CAP, *sc = big_raw + 2 * BIG_CAP;
+            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                const uint32_t si = gv[q0 + i];
+                sk[i] = skey[si];
+                sp[i] = w.spix[si];
+            }
+            __syncthreads();
+            const SweepView<true> V{sk, sp, sc, skey, w.spix, gv, q0};
+            sweep_block(V, n, dt, s_min);
+            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
+        } else {
+            if (threadIdx.x == 0) atomicAdd(&v.changed[2], 1u);   // diagnostics: swept from global memory
             const SweepView<false> V{nullptr, nullptr, v.cpar + q0, skey, w.spix, gv, q0};
-            sweep_component(V, n, dt, lane);
-            for (uint32_t i = lane; i < n; i += 32) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
+            sweep_block(V, n, dt, s_min);
+            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) w.parent[gv[q0 + i]] = gv[q0 + V.find(i)];
         }
-        __syncwarp();
+        __syncthreads();   // the staging is rewritten for the next component
     }
 }
 
@@ -382,6 +431,7 @@ __global__ void __launch_bounds__(256) k_pixel_latest(Work w, VarWork v) {
         if (d == 4) {   // the pixel itself: the previous hit of the timeline
             out[p0] = 0xFFFFFFFFu;
             for (uint32_t i = p0 + 1; i < p1; ++i) out[i] = tl[i - 1];
+            for (uint32_t i = p0; i < p1; ++i) v.cpar[tl[i]] = i;   // timeline index of each position
             continue;
         }
         const uint32_t q = (uint32_t)y * W + (uint32_t)x;
@@ -484,19 +534,21 @@ __device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep,
 }
 
 // A round over every hit's 9 latest neighbours (the first round, and any
-// round after an overflow), in pixel-timeline order: merges what the rule
-// allows, lists the rest.
+// round after an overflow), in (ToA, position) order, so that the forest
+// and key accesses of neighbouring threads are close and the open edges are
+// listed in time order: merges what the rule allows, lists the rest.  The
+// hit's timeline index (cpar, written by k_pixel_latest) locates its 9
+// entries.
 __global__ void __launch_bounds__(256) k_global_full(Work w, VarWork v, int out) {
     const Prob &P = *w.prob;
     const Seg &g = w.seg[0];
     const uint32_t *skey = w.keys[sorted_sel(P)];
-    const uint32_t *tl = v.v[v.prob->npasses & 1u] + g.off;
     const uint32_t n = g.n, dt = g.dt;
     bool changed = false;
     for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {   // whole warps: ballots
-        const uint32_t i = i0 + threadIdx.x;
-        const bool valid = i < n;
-        const uint32_t s = valid ? tl[i] : 0, ks = valid ? skey[s] : 0;
+        const bool valid = i0 + threadIdx.x < n;
+        const uint32_t s = g.off + i0 + threadIdx.x;
+        const uint32_t i = valid ? v.cpar[s] : 0, ks = valid ? skey[s] : 0;
         uint32_t rh = valid ? gfind(w.parent, s) : 0;
 #pragma unroll 1
         for (int d = 0; d < 9; ++d) {
@@ -575,7 +627,7 @@ void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L) {
     cudaMemsetAsync(v.changed, 0, 3 * sizeof(uint32_t), L.stream);
     k_static_sweep<<<L.fit(k_static_sweep, SW_WARPS * 32, 0), SW_WARPS * 32, 0, L.stream>>>(w, v);
     L.mark("k_static_sweep");
-    k_static_sweep_big<<<L.fit(k_static_sweep_big, 32, BIG_SMEM), 32, BIG_SMEM, L.stream>>>(w, v);
+    k_static_sweep_big<<<L.fit(k_static_sweep_big, BIG_THREADS, BIG_SMEM), BIG_THREADS, BIG_SMEM, L.stream>>>(w, v);
     L.mark("k_static_sweep_big");
 }
 

@@ -101,9 +101,9 @@ def test_device_paths_are_reached():
     assert st["rounds"] >= 3 and st["exact_checks"] >= 1, st
     rng = np.random.default_rng(31)
     same = random_hits(rng, 9000, 60, 40, 0)               # one ToA: every hit within dt of every other
-    st = _gpu_stats(same, 60, 40, 0, "static")            # 9000 hits within dt: past both windows
+    st = _gpu_stats(same, 60, 40, 0, "static")            # a 9000-hit component: the CTA sweep, global
     assert st["windowed"] > 0 and st["window_fallbacks"] == st["windowed"] == st["global_sweeps"], st
-    big = random_hits(rng, 3000, 60, 40, 0)                # 3000 within dt: past the first window only
+    big = random_hits(rng, 3000, 60, 40, 0)                # 3000 within dt: the CTA sweep, staged
     st = _gpu_stats(big, 60, 40, 0, "static")
     assert st["window_fallbacks"] > 0 and st["global_sweeps"] == 0, st
     # every pixel of a 30 x 30 sensor fires 20 times at random, far apart in
