@@ -357,6 +357,7 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
 // reset afterwards (Algorithm 3 step 7).
 constexpr int TAB_THREADS = 1024;
 constexpr uint16_t TAB_NONE = 0xFFFFu;
+constexpr uint32_t TAB_NONE32 = 0xFFFFFFFFu;   // a parent not written yet in this tile
 constexpr int TAB_WALK = 64;
 constexpr int TAB_EDGES = 3 * TILE / 2;
 constexpr int CAND = 6;
@@ -471,22 +472,36 @@ __device__ __forceinline__ void tab_walk(TabShared &S, uint32_t k, uint32_t key,
 }
 
 // Append the warp's candidate edges to the shared list; every lane calls
-// this (a ballot per candidate slot).
-__device__ __forceinline__ void tab_append(TabShared &S, uint32_t k, const uint32_t (&cand)[CAND], int nc,
+// this (a ballot per candidate slot).  Candidate c of a lane is listed if
+// bit c of its mask is set.
+__device__ __forceinline__ void tab_append(TabShared &S, uint32_t k, const uint32_t (&cand)[CAND], uint32_t keep,
                                            int lane) {
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const uint32_t most = __reduce_max_sync(0xffffffffu, (uint32_t)nc);
+    const uint32_t most = __reduce_or_sync(0xffffffffu, keep);
 #pragma unroll
     for (int c = 0; c < CAND; ++c) {
-        if (c >= (int)most) break;
-        const bool has = c < nc;
+        if (!(most >> c)) break;
+        const bool has = (keep >> c) & 1u;
         const uint32_t m = __ballot_sync(0xffffffffu, has);
+        if (!m) continue;
         uint32_t slot0 = 0;
         if (lane == 0) slot0 = atomicAdd(&S.nedges, (uint32_t)__popc(m));
         slot0 = __shfl_sync(0xffffffffu, slot0, 0);
         const uint32_t slot = slot0 + __popc(m & lt_mask);
         if (has && slot < TAB_EDGES) S.edges[slot] = (k << 16) | cand[c];
     }
+}
+
+// Candidates of hit k whose edge the parent links already imply: a
+// candidate c whose own parent is k's parent is in k's tree.  S.par holds
+// TAB_NONE until c's walk has written it (then the edge is kept).
+__device__ __forceinline__ uint32_t tab_keep(const TabShared &S, const uint32_t (&cand)[CAND], int nc,
+                                             uint32_t parent) {
+    uint32_t keep = 0;
+#pragma unroll
+    for (int c = 0; c < CAND; ++c)
+        if (c < nc && reinterpret_cast<const volatile uint32_t *>(S.par)[cand[c]] != parent) keep |= 1u << c;
+    return keep;
 }
 
 __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
@@ -525,6 +540,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
                 if (k < n_t) {
                     S.key[k] = kv[q];
+                    S.par[k] = TAB_NONE32;
                     S.next[k] = tab_push(S.tab, tab_pid(pv[q], W), (uint16_t)k);
                 }
             }
@@ -532,13 +548,14 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                uint32_t parent = k, cand[CAND];
+                uint32_t parent = k, cand[CAND], keep = 0;
                 int nc = 0;
                 if (k < n_t) {
                     tab_walk(S, k, kv[q], tab_pid(pv[q], W), W2, dt, parent, cand, nc);
-                    S.par[k] = parent;
+                    keep = tab_keep(S, cand, nc, parent);
+                    vpar[k] = parent;
                 }
-                tab_append(S, k, cand, nc, lane);
+                tab_append(S, k, cand, keep, lane);
             }
         } else {
             // band by band: a band's table holds its rows and the rows just
@@ -548,7 +565,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                if (k < n_t) { S.key[k] = kv[q]; S.pix[k] = pv[q]; }
+                if (k < n_t) { S.key[k] = kv[q]; S.pix[k] = pv[q]; S.par[k] = TAB_NONE32; }
             }
             __syncthreads();
             for (uint32_t b = 0; b < nb; ++b) {
@@ -571,7 +588,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 const uint32_t cnt = S.wl_count[b];
                 for (uint32_t base = 0; base < cnt; base += TAB_THREADS) {
                     const uint32_t idx = base + threadIdx.x;
-                    uint32_t k = 0, parent = 0, cand[CAND];
+                    uint32_t k = 0, parent = 0, cand[CAND], keep = 0;
                     int nc = 0;
                     if (idx < cnt) {
                         k = S.wl[idx];
@@ -579,9 +596,10 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                         const uint32_t pix = S.pix[k];
                         tab_walk(S, k, S.key[k], ((pix >> 16) + 1 - y0) * W2 + (pix & 0xFFFFu) + 1, W2, dt,
                                  parent, cand, nc);
-                        S.par[k] = parent;
+                        keep = tab_keep(S, cand, nc, parent);
+                        vpar[k] = parent;
                     }
-                    tab_append(S, k, cand, nc, lane);
+                    tab_append(S, k, cand, keep, lane);
                 }
                 __syncthreads();
 #pragma unroll
