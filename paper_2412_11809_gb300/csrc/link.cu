@@ -357,7 +357,6 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
 // reset afterwards (Algorithm 3 step 7).
 constexpr int TAB_THREADS = 1024;
 constexpr uint16_t TAB_NONE = 0xFFFFu;
-constexpr uint32_t TAB_NONE32 = 0xFFFFFFFFu;   // a parent not written yet in this tile
 constexpr int TAB_WALK = 64;
 constexpr int TAB_EDGES = 3 * TILE / 2;
 constexpr int CAND = 6;
@@ -492,18 +491,6 @@ __device__ __forceinline__ void tab_append(TabShared &S, uint32_t k, const uint3
     }
 }
 
-// Candidates of hit k whose edge the parent links already imply: a
-// candidate c whose own parent is k's parent is in k's tree.  S.par holds
-// TAB_NONE until c's walk has written it (then the edge is kept).
-__device__ __forceinline__ uint32_t tab_keep(const TabShared &S, const uint32_t (&cand)[CAND], int nc,
-                                             uint32_t parent) {
-    uint32_t keep = 0;
-#pragma unroll
-    for (int c = 0; c < CAND; ++c)
-        if (c < nc && reinterpret_cast<const volatile uint32_t *>(S.par)[cand[c]] != parent) keep |= 1u << c;
-    return keep;
-}
-
 __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     extern __shared__ __align__(16) unsigned char tab_raw[];
     TabShared &S = *reinterpret_cast<TabShared *>(tab_raw);
@@ -540,7 +527,6 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
                 if (k < n_t) {
                     S.key[k] = kv[q];
-                    S.par[k] = TAB_NONE32;
                     S.next[k] = tab_push(S.tab, tab_pid(pv[q], W), (uint16_t)k);
                 }
             }
@@ -552,8 +538,8 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 int nc = 0;
                 if (k < n_t) {
                     tab_walk(S, k, kv[q], tab_pid(pv[q], W), W2, dt, parent, cand, nc);
-                    keep = tab_keep(S, cand, nc, parent);
-                    vpar[k] = parent;
+                    keep = (1u << nc) - 1u;
+                    S.par[k] = parent;
                 }
                 tab_append(S, k, cand, keep, lane);
             }
@@ -565,7 +551,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                if (k < n_t) { S.key[k] = kv[q]; S.pix[k] = pv[q]; S.par[k] = TAB_NONE32; }
+                if (k < n_t) { S.key[k] = kv[q]; S.pix[k] = pv[q]; }
             }
             __syncthreads();
             for (uint32_t b = 0; b < nb; ++b) {
@@ -596,8 +582,8 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                         const uint32_t pix = S.pix[k];
                         tab_walk(S, k, S.key[k], ((pix >> 16) + 1 - y0) * W2 + (pix & 0xFFFFu) + 1, W2, dt,
                                  parent, cand, nc);
-                        keep = tab_keep(S, cand, nc, parent);
-                        vpar[k] = parent;
+                        keep = (1u << nc) - 1u;
+                        S.par[k] = parent;
                     }
                     tab_append(S, k, cand, keep, lane);
                 }

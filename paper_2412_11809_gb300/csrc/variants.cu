@@ -408,69 +408,41 @@ __global__ void __launch_bounds__(1024) k_pixel_scan(Work w, VarWork v) {
 
 // (b), once before the rounds: for every hit and each of its 9 pixels the
 // latest earlier hit there, or none.  Hits grouped by pixel (timelines, each
-// in (ToA, position) order) are cut into chunks of LATEST_CHUNK entries; one
-// thread per (chunk, direction) walks its chunk with a pointer into the
-// neighbour pixel's timeline (placed by a binary search where the chunk
-// enters a pixel), so each hit's latest earlier hit there is where the
-// pointer stops (the pixel itself: the previous entry).  Results are stored
-// in timeline order, latest[d * stride + i] for the hit at timeline index i,
-// so each thread writes a contiguous run; k_pixel_index records each
-// position's timeline index.
-constexpr uint32_t LATEST_CHUNK = 256;
-
+// in (ToA, position) order) are taken in timeline order, a thread per hit and
+// direction, the hit's pixel from the grouping sort's keys: the latest
+// earlier hit on the neighbour pixel is found by a binary search in that
+// pixel's timeline (the lanes of a warp search the same timeline for nearby
+// values, so their probes mostly hit the same lines; the pixel itself: the
+// previous entry).  Results are stored in timeline order, latest[d * stride
+// + i] for the hit at timeline index i (coalesced); the d = 4 pass also
+// records each position's timeline index (cpar).
 __global__ void __launch_bounds__(256) k_pixel_latest(Work w, VarWork v) {
     const Seg &g = w.seg[0];
-    const uint32_t W = g.width, H = g.height, np = W * H, n = g.n;
-    const uint32_t *tl = v.v[v.prob->npasses & 1u] + g.off;   // sorted positions grouped by pixel
+    const uint32_t W = g.width, H = g.height, n = g.n;
+    const uint32_t sel = v.prob->npasses & 1u;
+    const uint32_t *tl = v.v[sel] + g.off;   // sorted positions grouped by pixel
+    const uint32_t *tk = v.k[sel] + g.off;   // their pixel ids
     const uint32_t *ps = v.pix_start;
-    const uint32_t chunks = (n + LATEST_CHUNK - 1) / LATEST_CHUNK, tasks = 9u * chunks;
+    const uint32_t tasks = 9u * n;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
-        const uint32_t d = t / chunks, c = t - d * chunks;
-        const uint32_t i0 = c * LATEST_CHUNK, i1 = i0 + LATEST_CHUNK < n ? i0 + LATEST_CHUNK : n;
-        uint32_t *out = v.latest + (size_t)d * v.lat_stride;
-        // the pixel whose timeline holds entry i0: the last p with ps[p] <= i0
-        uint32_t lo = 0, hi = np - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (ps[mid] <= i0) lo = mid; else hi = mid - 1;
+        const uint32_t d = t / n, i = t - d * n;
+        const uint32_t s = tl[i], p = tk[i];
+        const int x = (int)(p % W) + (int)(d % 3) - 1, y = (int)(p / W) + (int)(d / 3) - 1;
+        uint32_t L = 0xFFFFFFFFu;
+        if (d == 4) {
+            if (i > ps[p]) L = tl[i - 1];
+            v.cpar[s] = i;   // timeline index of each position
+        } else if (x >= 0 && x < (int)W && y >= 0 && y < (int)H) {
+            const uint32_t q = (uint32_t)y * W + (uint32_t)x;
+            const uint32_t q0 = ps[q];
+            uint32_t a = q0, b = ps[q + 1];   // first entry of q's timeline at or after s
+            while (a < b) {
+                const uint32_t mid = (a + b) >> 1;
+                if (tl[mid] < s) a = mid + 1; else b = mid;
+            }
+            if (a > q0) L = tl[a - 1];
         }
-        uint32_t p = lo, p_end = ps[p + 1];
-        uint32_t j = 0, q1 = 0, q0 = 0;
-        bool outside = true;
-        for (uint32_t i = i0; i < i1; ++i) {
-            const bool enter = i == i0 || i == p_end;
-            if (i == p_end) {   // the next non-empty timeline
-                while (ps[p + 1] == i) ++p;
-                p_end = ps[p + 1];
-            }
-            const uint32_t s = tl[i];
-            if (enter) {
-                const int x = (int)(p % W) + (int)(d % 3) - 1, y = (int)(p / W) + (int)(d / 3) - 1;
-                outside = x < 0 || x >= (int)W || y < 0 || y >= (int)H;
-                if (!outside && d != 4) {
-                    const uint32_t q = (uint32_t)y * W + (uint32_t)x;
-                    q0 = ps[q];
-                    q1 = ps[q + 1];
-                    uint32_t a = q0, b = q1;   // first entry of q's timeline at or after s
-                    while (a < b) {
-                        const uint32_t mid = (a + b) >> 1;
-                        if (tl[mid] < s) a = mid + 1; else b = mid;
-                    }
-                    j = a;
-                }
-            }
-            uint32_t L = 0xFFFFFFFFu;
-            if (outside) {
-                L = 0xFFFFFFFFu;
-            } else if (d == 4) {
-                L = i > ps[p] ? tl[i - 1] : 0xFFFFFFFFu;
-            } else {
-                while (j < q1 && tl[j] < s) ++j;
-                L = j > q0 ? tl[j - 1] : 0xFFFFFFFFu;
-            }
-            out[i] = L;
-            if (d == 4) v.cpar[s] = i;   // timeline index of each position
-        }
+        v.latest[(size_t)d * v.lat_stride + i] = L;
     }
 }
 
