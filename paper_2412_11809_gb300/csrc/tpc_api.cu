@@ -232,6 +232,7 @@ struct VarSpace {
         v.latest = mem.alloc<uint32_t>(9 * positions, e);
         v.lat_stride = (uint32_t)positions;
         v.changed = mem.alloc<uint32_t>(4, e);
+        v.ecount = mem.alloc<unsigned long long>(2, e);
         // open (b) edges: 4 per position per list; a round that finds more
         // marks the overflow and the next round reads every hit's 9 again
         v.edge_cap = (uint32_t)std::min<size_t>(4 * positions, 0xFFFFFFFFull);

@@ -145,8 +145,10 @@ struct VarWork {
     uint32_t *latest;          // (b): [9][lat_stride]: for the hit at each pixel-timeline index, the
                                //      latest earlier hit (sorted position) on each neighbour pixel
     uint32_t lat_stride;       // (b): entries per direction of latest
-    uint32_t *changed;         // (b): [0] a round merged something, [1] the edge list overflowed,
-                               //      [2], [3] entries in edge lists 0 and 1
+    uint32_t *changed;         // (b): [0] a round merged something, [1] the edge list overflowed;
+                               // (c): [0] windowed components, [1] of those swept again by a CTA,
+                               //      [2] of those swept from global memory
+    unsigned long long *ecount;  // (b): edges pushed to lists 0 and 1 (beyond edge_cap: overflow)
     uint2 *edges[2];           // (b): edges (hit, latest neighbour) not merged yet, ping-pong
     uint32_t edge_cap;         // (b): entries each edge list holds
     uint32_t *work;            // (c): next chunk of the grouped order to sweep

@@ -423,9 +423,9 @@ __global__ void __launch_bounds__(256) k_pixel_latest(Work w, VarWork v) {
     const uint32_t *tl = v.v[sel] + g.off;   // sorted positions grouped by pixel
     const uint32_t *tk = v.k[sel] + g.off;   // their pixel ids
     const uint32_t *ps = v.pix_start;
-    const uint32_t tasks = 9u * n;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
-        const uint32_t d = t / n, i = t - d * n;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t d = 0; d < 9; ++d)   // 9 n can exceed 32 bits: directions outside
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t s = tl[i], p = tk[i];
         const int x = (int)(p % W) + (int)(d % 3) - 1, y = (int)(p / W) + (int)(d / 3) - 1;
         uint32_t L = 0xFFFFFFFFu;
@@ -519,10 +519,10 @@ __device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep,
     const uint32_t m = __ballot_sync(0xffffffffu, keep);
     if (!m) return;
     const int lane = threadIdx.x & 31;
-    uint32_t base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(&v.changed[2 + out], (uint32_t)__popc(m));
+    unsigned long long base = 0;   // 64 bits: a full round can push more than 2^32 edges
+    if (lane == __ffs(m) - 1) base = atomicAdd(&v.ecount[out], (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    const uint32_t slot = base + __popc(m & ((1u << lane) - 1u));
+    const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
     if (keep) {
         if (slot < v.edge_cap) v.edges[out][slot] = make_uint2(s, l);
         else v.changed[1] = 1u;
@@ -563,8 +563,8 @@ __global__ void __launch_bounds__(256) k_global_list(Work w, VarWork v, int in) 
     const Prob &P = *w.prob;
     const uint32_t *skey = w.keys[sorted_sel(P)];
     const uint32_t dt = w.seg[0].dt;
-    const uint32_t n = v.changed[2 + in];
-    const uint32_t cnt = n < v.edge_cap ? n : v.edge_cap;
+    const unsigned long long n = v.ecount[in];
+    const uint32_t cnt = n < v.edge_cap ? (uint32_t)n : v.edge_cap;
     bool changed = false;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < cnt; e0 += stride) {
@@ -593,7 +593,7 @@ void launch_group_last(const Work &w, const VarWork &v, const Launch &L) {
 void launch_global_edges(const Work &w, const VarWork &v, int full, int in, const Launch &L) {
     const int out = full ? 0 : 1 - in;
     cudaMemsetAsync(v.changed, 0, 2 * sizeof(uint32_t), L.stream);
-    cudaMemsetAsync(v.changed + 2 + out, 0, sizeof(uint32_t), L.stream);
+    cudaMemsetAsync(v.ecount + out, 0, sizeof(unsigned long long), L.stream);
     if (full) {
         k_global_full<<<L.fit(k_global_full, 256, 0), 256, 0, L.stream>>>(w, v, out);
         L.mark("k_global_full");
