@@ -120,6 +120,14 @@ def test_fullsize_448x512_all_variants(stream):
         for dt in (128, 384):
             lab, rec = _gpu(d_hits, dt, "local")
             assert _check_local_sampled(hits, win, lab, rec, dt, rng) >= N_SAMPLES // 2
+            if dt == 128:   # and every label against the temporal-split CPU method (cpu_baseline,
+                # bit-exact against the oracle in the CPU suite), a few seconds on the host cores
+                import os
+                import cpu_baseline
+                want, wrec, _ = cpu_baseline.cluster(hits, W, H, dt, 6400, max(1, len(os.sched_getaffinity(0))))
+                np.testing.assert_array_equal(lab, want)
+                assert_features_equal(rec, wrec)
+                del want, wrec
             del lab, rec
         del d_hits
     finally:

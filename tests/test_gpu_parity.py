@@ -217,6 +217,14 @@ def test_cfg1_full_size_sampled():
     checked = sampled_cluster_check(hits, lab, 256, 256, synth.DT_200NS, 150,
                                     np.random.default_rng(1))
     assert checked > 50
+    # every label and record against the paper's temporal-split CPU method
+    # (cpu_baseline, itself bit-exact against the oracle in the CPU suite),
+    # which clusters the whole stream in a few seconds on the host cores
+    import os
+    import cpu_baseline
+    want, rec, _ = cpu_baseline.cluster(hits, 256, 256, synth.DT_200NS, 6400, max(1, len(os.sched_getaffinity(0))))
+    np.testing.assert_array_equal(lab, want)
+    assert_features_equal(feats, rec)
 
 
 def test_labels_async_and_two_context_pipeline():
