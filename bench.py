@@ -703,6 +703,22 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # launch choices for this workload from the autotuner (tpc_tune_batch on
+    # the one-context batch; cached per GPU, sensor and size bucket), then
+    # the warm-up steps with them
+    tuning = None
+    if not args.no_tune:
+        import tempfile
+        from paper_2412_11809_gb300 import tune_batch
+        c.push(d_hits)
+        t0 = time.perf_counter()
+        rep = tune_batch([c], os.path.join(tempfile.gettempdir(), "tpc_tune_cache.txt"))
+        c.flush()    # the tuner leaves the hits pending
+        c.sync()
+        tuning = {"chosen": rep.chosen.as_dict(), "from_cache": bool(rep.from_cache), "trials": rep.trials,
+                  "untuned_ms": rep.untuned_ms, "tuned_ms": rep.tuned_ms,
+                  "seconds": time.perf_counter() - t0, "key": rep.key.decode()}
+
     with ClockSampler(local) as clocks:
         for _ in range(args.warmup):
             n_clusters = step_device()
@@ -751,6 +767,8 @@ def run_gpu(args):
     pin_in = host_u8.pin_memory()
     streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(NCTX - 1)]
     ctxs = [c] + [Clusterer(W, H, DT, stream=st) for st in streams[1:]]
+    for cx in ctxs[1:]:
+        cx.set_tuning(c.tuning())   # the same launch choices as the device-resident steps
     pin_lab = [torch.empty(n, dtype=torch.int64).pin_memory() for _ in ctxs]
     rec_cap = max(1, n // 4)   # cluster records (about 5 % of the hits here)
     pin_rec = [torch.empty((rec_cap, CLUSTER_DTYPE.itemsize), dtype=torch.uint8).pin_memory() for _ in ctxs]
@@ -863,6 +881,7 @@ def run_gpu(args):
                                 "traffic": stored_traffic(dominant, n)},
             "issue_roofline": issue,
             "kernel_ms": prof_ms,
+            "launch_choices": tuning,
             "forest_depth": depth,
             "cpu_baseline": cpu,
             "cpu_parallel": cpu_par,
@@ -895,6 +914,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4 * 2**20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, serving, large-sensor and ingest lines")
+    ap.add_argument("--no-tune", action="store_true", help="default launch choices instead of the autotuner's")
     ap.add_argument("--serving-hits", type=int, default=4 * 2**20, help="base hits per serving stream")
     ap.add_argument("--serving-chunks", type=int, default=1024)
     ap.add_argument("--serving-budget", type=int, default=3 << 30,

@@ -230,6 +230,7 @@ struct VarSpace {
         v.glast = mem.alloc<uint32_t>(positions, e);
         v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
         v.latest = mem.alloc<uint32_t>(9 * positions, e);
+        v.lat_stride = (uint32_t)positions;
         v.changed = mem.alloc<uint32_t>(4, e);
         v.ecount = mem.alloc<unsigned long long>(2, e);
         // open (b) edges: 4 per position per list; a round that finds more

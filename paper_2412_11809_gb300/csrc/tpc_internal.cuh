@@ -139,10 +139,12 @@ struct Work {
 // Extra arrays of the (b)/(c) variants (single-segment steps only).
 struct VarWork {
     uint32_t *k[2], *v[2];     // grouping radix sort: keys / sorted positions
-    uint32_t *cpar;            // (c): forest over the root-grouped order
+    uint32_t *cpar;            // (c): forest over the root-grouped order; (b): timeline index of each position
     uint32_t *glast;           // (b): per root, last key of its group
     uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
-    uint32_t *latest;          // (b): per position, 9 slots: latest earlier hit on each neighbour pixel
+    uint32_t *latest;          // (b): [9][lat_stride]: for the hit at each pixel-timeline index, the
+                               //      latest earlier hit (sorted position) on each neighbour pixel
+    uint32_t lat_stride;       // (b): entries per direction of latest
     uint32_t *changed;         // (b): [0] a round merged something, [1] the edge list overflowed;
                                // (c): [0] windowed components, [1] of those swept again by a CTA,
                                //      [2] of those swept from global memory

@@ -408,14 +408,14 @@ __global__ void __launch_bounds__(1024) k_pixel_scan(Work w, VarWork v) {
 
 // (b), once before the rounds: for every hit and each of its 9 pixels the
 // latest earlier hit there, or none.  Hits grouped by pixel (timelines, each
-// in (ToA, position) order) are taken in timeline order, one thread per hit,
-// the hit's pixel from the grouping sort's keys: the latest earlier hit on a
-// neighbour pixel is found by a binary search in that pixel's timeline (the
-// lanes of a warp search the same timelines for nearby values, so their
-// probes mostly hit the same lines; the pixel itself: the previous entry).
-// The 9 results go to the hit's 36-byte record latest[p * 9 + d] at its
-// position p: one scattered but whole record per hit, which the rounds then
-// read in position order.
+// in (ToA, position) order) are taken in timeline order, a thread per hit and
+// direction, the hit's pixel from the grouping sort's keys: the latest
+// earlier hit on the neighbour pixel is found by a binary search in that
+// pixel's timeline (the lanes of a warp search the same timeline for nearby
+// values, so their probes mostly hit the same lines; the pixel itself: the
+// previous entry).  Results are stored in timeline order, latest[d * stride
+// + i] for the hit at timeline index i (coalesced); the d = 4 pass also
+// records each position's timeline index (cpar).
 __global__ void __launch_bounds__(256) k_pixel_latest(Work w, VarWork v) {
     const Seg &g = w.seg[0];
     const uint32_t W = g.width, H = g.height, n = g.n;
@@ -423,31 +423,26 @@ __global__ void __launch_bounds__(256) k_pixel_latest(Work w, VarWork v) {
     const uint32_t *tl = v.v[sel] + g.off;   // sorted positions grouped by pixel
     const uint32_t *tk = v.k[sel] + g.off;   // their pixel ids
     const uint32_t *ps = v.pix_start;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t d = 0; d < 9; ++d)   // 9 n can exceed 32 bits: directions outside
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t s = tl[i], p = tk[i];
-        const int px = (int)(p % W), py = (int)(p / W);
-        uint32_t out[9];
-#pragma unroll
-        for (int d = 0; d < 9; ++d) {
-            const int x = px + d % 3 - 1, y = py + d / 3 - 1;
-            uint32_t L = 0xFFFFFFFFu;
-            if (d == 4) {
-                if (i > ps[p]) L = tl[i - 1];
-            } else if (x >= 0 && x < (int)W && y >= 0 && y < (int)H) {
-                const uint32_t q = (uint32_t)y * W + (uint32_t)x;
-                const uint32_t q0 = ps[q];
-                uint32_t a = q0, b = ps[q + 1];   // first entry of q's timeline at or after s
-                while (a < b) {
-                    const uint32_t mid = (a + b) >> 1;
-                    if (tl[mid] < s) a = mid + 1; else b = mid;
-                }
-                if (a > q0) L = tl[a - 1];
+        const int x = (int)(p % W) + (int)(d % 3) - 1, y = (int)(p / W) + (int)(d / 3) - 1;
+        uint32_t L = 0xFFFFFFFFu;
+        if (d == 4) {
+            if (i > ps[p]) L = tl[i - 1];
+            v.cpar[s] = i;   // timeline index of each position
+        } else if (x >= 0 && x < (int)W && y >= 0 && y < (int)H) {
+            const uint32_t q = (uint32_t)y * W + (uint32_t)x;
+            const uint32_t q0 = ps[q];
+            uint32_t a = q0, b = ps[q + 1];   // first entry of q's timeline at or after s
+            while (a < b) {
+                const uint32_t mid = (a + b) >> 1;
+                if (tl[mid] < s) a = mid + 1; else b = mid;
             }
-            out[d] = L;
+            if (a > q0) L = tl[a - 1];
         }
-        uint32_t *rec = v.latest + (size_t)(s - g.off) * 9;
-#pragma unroll
-        for (int d = 0; d < 9; ++d) rec[d] = out[d];
+        v.latest[(size_t)d * v.lat_stride + i] = L;
     }
 }
 
@@ -537,7 +532,9 @@ __device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep,
 // A round over every hit's 9 latest neighbours (the first round, and any
 // round after an overflow), in (ToA, position) order, so that the forest
 // and key accesses of neighbouring threads are close and the open edges are
-// listed in time order: merges what the rule allows, lists the rest.
+// listed in time order: merges what the rule allows, lists the rest.  The
+// hit's timeline index (cpar, written by k_pixel_latest) locates its 9
+// entries.
 __global__ void __launch_bounds__(256) k_global_full(Work w, VarWork v, int out) {
     const Prob &P = *w.prob;
     const Seg &g = w.seg[0];
@@ -546,12 +543,12 @@ __global__ void __launch_bounds__(256) k_global_full(Work w, VarWork v, int out)
     bool changed = false;
     for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {   // whole warps: ballots
         const bool valid = i0 + threadIdx.x < n;
-        const uint32_t s = g.off + i0 + threadIdx.x, i = i0 + threadIdx.x;
-        const uint32_t ks = valid ? skey[s] : 0;
+        const uint32_t s = g.off + i0 + threadIdx.x;
+        const uint32_t i = valid ? v.cpar[s] : 0, ks = valid ? skey[s] : 0;
         uint32_t rh = valid ? gfind(w.parent, s) : 0;
 #pragma unroll 1
         for (int d = 0; d < 9; ++d) {
-            const uint32_t l = valid ? v.latest[(size_t)i * 9 + d] : 0xFFFFFFFFu;
+            const uint32_t l = valid ? v.latest[(size_t)d * v.lat_stride + i] : 0xFFFFFFFFu;
             int r = 0;
             if (l != 0xFFFFFFFFu) r = global_edge(w, v, ks, dt, s, rh, l);
             changed |= r == 1;

@@ -124,10 +124,11 @@ def test_fullsize_448x512_all_variants(stream):
                 # bit-exact against the oracle in the CPU suite), a few seconds on the host cores
                 import os
                 import cpu_baseline
-                want, wrec, _ = cpu_baseline.cluster(hits, W, H, dt, 6400, max(1, len(os.sched_getaffinity(0))))
-                np.testing.assert_array_equal(lab, want)
-                assert_features_equal(rec, wrec)
-                del want, wrec
+                ts_lab, ts_rec, _ = cpu_baseline.cluster(hits, W, H, dt, 6400,
+                                                         max(1, len(os.sched_getaffinity(0))))
+                np.testing.assert_array_equal(lab, ts_lab)
+                assert_features_equal(rec, ts_rec)
+                del ts_lab, ts_rec
             del lab, rec
         del d_hits
     finally:
