@@ -4,8 +4,9 @@ Workload (one step): the high-flux 256x256 sensor stream — 64 Mi hits at
 40 Mhits/s, 80 % random-walk blobs / 20 % straight tracks of 10-300 pixels,
 dead-time refires, window-shuffled by up to 1000 positions — clustered with
 the edge-connectivity variant at dt = 128 ticks (200 ns), plus per-cluster
-features and compaction.  One step = tpc_push (device) + tpc_flush +
-tpc_labels + tpc_cluster_features into caller device buffers.
+features and compaction.  One step = tpc_push (device) + tpc_flush writing
+labels and records into caller device buffers (tpc_bind_outputs) +
+tpc_counts (waits for the step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -692,11 +693,13 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     c = Clusterer(W, H, DT, stream=stream)
 
+    # the step writes labels and records straight into these caller buffers
+    c.bind_outputs(d_labels.data_ptr(), d_rec.data_ptr(), n)
+
     def step_device():
         c.push(d_hits)
         c.flush()
-        c.labels_into(d_labels.data_ptr(), n, device=True)
-        return c.features_into(d_rec.data_ptr(), n, device=True)
+        return c.counts()[1]   # waits for the step; its labels and records are in place
 
     def barrier():
         if world > 1:
@@ -764,6 +767,7 @@ def run_gpu(args):
     # (tpc_labels_async), and its records are fetched NCTX - 1 steps later
     # (fetching them returns their count, which waits for that step).
     NCTX = 3
+    c.bind_outputs(None, None)   # the end-to-end steps copy results out to host memory
     pin_in = host_u8.pin_memory()
     streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(NCTX - 1)]
     ctxs = [c] + [Clusterer(W, H, DT, stream=st) for st in streams[1:]]

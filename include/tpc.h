@@ -160,6 +160,22 @@ int tpc_labels(tpc_ctx *ctx, uint64_t *labels, uint64_t *indices, size_t cap,
    TPC_ERR_CAP (nothing queued) if cap < *n_out. */
 int tpc_labels_async(tpc_ctx *ctx, uint64_t *labels, size_t cap, size_t *n_out, int where);
 
+/* Bind caller device buffers (memory of the context's device) that every
+   following one-shot step of the context (tpc_flush of a non-streaming
+   context, any variant, or a tpc_batch_flush it takes part in) writes its
+   results into directly: labels[i] for the i-th hit pushed since the
+   previous step, records[k] ordered by label, cap entries each, so that no
+   retrieval copy is needed (tpc_counts gives the cluster count; tpc_labels
+   and tpc_cluster_features still work, copying from these buffers).  A
+   step with more hits than cap fails with TPC_ERR_CAP before doing
+   anything (the hits stay pending); more clusters than cap is reported as
+   TPC_ERR_NOMEM by tpc_sync, as for the context's own buffers.  The caller
+   keeps the buffers alive and unread until the step's work is done (after
+   tpc_sync or a retrieval call).  labels = records = NULL unbinds.
+   TPC_ERR_ARG for host or foreign-device pointers, one NULL of two or cap
+   0; TPC_ERR_STATE for a streaming context. */
+int tpc_bind_outputs(tpc_ctx *ctx, uint64_t *labels, tpc_cluster *records, size_t cap);
+
 /* Cluster records finalised by the last processing step, ordered by label.
    Same size protocol as tpc_labels. */
 int tpc_cluster_features(tpc_ctx *ctx, tpc_cluster *out, size_t cap, size_t *n_out,

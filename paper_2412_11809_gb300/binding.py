@@ -72,6 +72,7 @@ SIGNATURES = {
     "tpc_tune_cache_lookup": ([ctypes.c_char_p, ctypes.c_char_p, _VP, ctypes.POINTER(ctypes.c_double)], _INT),
     "tpc_tune_cache_store": ([ctypes.c_char_p, ctypes.c_char_p, _VP, ctypes.c_double], _INT),
     "tpc_variant_stats_get": ([_VP, _VP], _INT),
+    "tpc_bind_outputs": ([_VP, _VP, _VP, _SZ], _INT),
     "tpc_strerror": ([_INT], ctypes.c_char_p),
     "tpc_destroy": ([_VP], None),
 }
@@ -326,6 +327,11 @@ class Clusterer:
         t = Tuning()
         _check(self._lib.tpc_get_tuning(self._h, ctypes.byref(t)), "tpc_get_tuning")
         return t
+
+    def bind_outputs(self, labels_ptr: int | None, records_ptr: int | None, cap: int = 0):
+        """``tpc_bind_outputs``: device buffers every following one-shot step
+        writes its labels and records into (None, None unbinds)."""
+        _check(self._lib.tpc_bind_outputs(self._h, labels_ptr, records_ptr, cap), "tpc_bind_outputs")
 
     def variant_stats(self) -> dict:
         """``tpc_variant_stats_get``: diagnostics of the last (b)/(c) flush."""

@@ -310,6 +310,13 @@ struct tpc_ctx {
     DevMem outmem;                 // output buffers
     uint64_t *d_labels = nullptr, *d_index = nullptr;
     tpc_cluster *d_rec = nullptr;
+    // caller device buffers one-shot steps write into (tpc_bind_outputs)
+    uint64_t *bound_labels = nullptr;
+    tpc_cluster *bound_rec = nullptr;
+    size_t bound_cap = 0;
+    // where the last step's labels and records are
+    uint64_t *res_labels = nullptr;
+    tpc_cluster *res_rec = nullptr;
     size_t out_cap = 0;
 
     // where the last step's results live: the own workspace after a flush or
@@ -477,6 +484,15 @@ cudaError_t run_step(tpc_ctx *owner, Workspace &ws, int nsegs, cudaStream_t st, 
     return cudaGraphLaunch(owner->graph, st);
 }
 
+// Outputs of a one-shot step: the caller's bound buffers, else the
+// context's own; the retrieval calls read them from where they went.
+void set_outputs(tpc_ctx *c, Seg &s) {
+    const bool bound = c->bound_labels != nullptr;
+    s.out_labels = c->res_labels = bound ? c->bound_labels : c->d_labels;
+    s.out_rec = c->res_rec = bound ? c->bound_rec : c->d_rec;
+    s.out_cap = (uint32_t)(bound ? c->bound_cap : c->out_cap);
+}
+
 // Whether a sensor takes k_tile_link instead of the table kernel under the
 // launch choices t (bit 0: single-band sensors, bit 1: banded ones).
 uint32_t link_general(const Tuning &t, uint32_t W, uint32_t H) {
@@ -613,9 +629,9 @@ int stream_step(tpc_ctx *c, size_t n, bool close_all) {
     s.carry_out = c->sbuf[c->scur];
     s.carry_gidx_out = c->sgidx[c->scur];
     s.ss = c->ss;
-    s.out_labels = c->d_labels;
+    s.out_labels = c->res_labels = c->d_labels;
     s.out_index = c->d_index;
-    s.out_rec = c->d_rec;
+    s.out_rec = c->res_rec = c->d_rec;
     s.out_cap = (uint32_t)c->out_cap;
     s.gidx_base = c->pushed;
     s.max_disorder = close_all ? ~0ull : c->max_disorder;
@@ -783,16 +799,15 @@ int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
 static int flush_variant(tpc_ctx *c, Tracer *tr) {
     const size_t n = c->pending;
     c->has_result = false;   // the workspace may move: the last result is gone
+    if (c->bound_labels && n > c->bound_cap) return TPC_ERR_CAP;
     if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
     if (c->vs.ensure(c->ws.pos_cap, (size_t)c->width * c->height) != cudaSuccess) return TPC_ERR_NOMEM;
-    if (ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (!c->bound_labels && ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
     if (!c->h_flag && host_alloc(&c->fail_alloc, (void **)&c->h_flag, 4 * sizeof(uint32_t)) != cudaSuccess)
         return TPC_ERR_NOMEM;
     Seg s = base_seg(c);
     s.hits = c->zc ? c->zc : c->in;
-    s.out_labels = c->d_labels;
-    s.out_rec = c->d_rec;
-    s.out_cap = (uint32_t)c->out_cap;
+    set_outputs(c, s);
     s.gidx_base = c->pushed;
     s.n_new = (uint32_t)n;
     if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
@@ -884,13 +899,12 @@ static int flush_impl(tpc_ctx *c, Tracer *tr) {
     c->has_result = false;   // the workspace may move: the last result is gone
     if (over_budget(c, c->ws.bytes_after(n) > c->ws.mem.bytes ? c->ws.bytes_after(n) - c->ws.mem.bytes : 0))
         return TPC_ERR_BUSY;
+    if (c->bound_labels && n > c->bound_cap) return TPC_ERR_CAP;
     if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
-    if (ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (!c->bound_labels && ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
     Seg s = base_seg(c);
     s.hits = c->zc ? c->zc : c->in;
-    s.out_labels = c->d_labels;
-    s.out_rec = c->d_rec;
-    s.out_cap = (uint32_t)c->out_cap;
+    set_outputs(c, s);
     s.gidx_base = c->pushed;
     s.n_new = (uint32_t)n;
     if (upload_segs(c, c->ws.w, &s, 1, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
@@ -965,7 +979,9 @@ int tpc_labels(tpc_ctx *c, uint64_t *labels, uint64_t *indices, size_t cap, size
     if (n && !labels) return TPC_ERR_ARG;
     if (!n) return TPC_OK;
     const cudaMemcpyKind kind = where == TPC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    if (cudaMemcpyAsync(labels, c->d_labels, n * sizeof(uint64_t), kind, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (labels != c->res_labels &&
+        cudaMemcpyAsync(labels, c->res_labels, n * sizeof(uint64_t), kind, c->stream) != cudaSuccess)
+        return TPC_ERR_CUDA;
     if (indices) {
         if (c->res_streaming) {
             if (cudaMemcpyAsync(indices, c->d_index, n * sizeof(uint64_t), kind, c->stream) != cudaSuccess)
@@ -989,7 +1005,8 @@ int tpc_labels_async(tpc_ctx *c, uint64_t *labels, size_t cap, size_t *n_out, in
     if (!n) return TPC_OK;
     if (!labels) return TPC_ERR_ARG;
     const cudaMemcpyKind kind = where == TPC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    return cudaMemcpyAsync(labels, c->d_labels, n * sizeof(uint64_t), kind, c->stream) == cudaSuccess
+    if (labels == c->res_labels) return TPC_OK;   // written there by the step
+    return cudaMemcpyAsync(labels, c->res_labels, n * sizeof(uint64_t), kind, c->stream) == cudaSuccess
                ? TPC_OK : TPC_ERR_CUDA;
 }
 
@@ -1005,7 +1022,9 @@ int tpc_cluster_features(tpc_ctx *c, tpc_cluster *out, size_t cap, size_t *n_out
     if (n && !out) return TPC_ERR_ARG;
     if (!n) return TPC_OK;
     const cudaMemcpyKind kind = where == TPC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    if (cudaMemcpyAsync(out, c->d_rec, n * sizeof(tpc_cluster), kind, c->stream) != cudaSuccess) return TPC_ERR_CUDA;
+    if (out != c->res_rec &&
+        cudaMemcpyAsync(out, c->res_rec, n * sizeof(tpc_cluster), kind, c->stream) != cudaSuccess)
+        return TPC_ERR_CUDA;
     return cudaStreamSynchronize(c->stream) == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }
 
@@ -1031,7 +1050,9 @@ int tpc::batch_step(tpc_ctx **ctxs, int n, bool consume) {
     // every context's pending copies and allocations must land before the
     // lead stream uses them
     for (int i = 0; i < n; ++i)
-        if (ensure_out(ctxs[i], ctxs[i]->pending) != cudaSuccess) return TPC_ERR_NOMEM;
+        if (ctxs[i]->bound_labels && ctxs[i]->pending > ctxs[i]->bound_cap) return TPC_ERR_CAP;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]->bound_labels && ensure_out(ctxs[i], ctxs[i]->pending) != cudaSuccess) return TPC_ERR_NOMEM;
     for (int i = 1; i < n; ++i) {
         if (cudaEventRecord(ctxs[i]->done_ev, ctxs[i]->stream) != cudaSuccess ||
             cudaStreamWaitEvent(lead->stream, ctxs[i]->done_ev, 0) != cudaSuccess)
@@ -1049,9 +1070,7 @@ int tpc::batch_step(tpc_ctx **ctxs, int n, bool consume) {
         tpc_ctx *c = ctxs[perm[k]];
         Seg s = base_seg(c, t);
         s.hits = c->zc ? c->zc : c->in;
-        s.out_labels = c->d_labels;
-        s.out_rec = c->d_rec;
-        s.out_cap = (uint32_t)c->out_cap;
+        set_outputs(c, s);
         s.gidx_base = c->pushed;
         s.n_new = (uint32_t)c->pending;
         segs[k] = s;
@@ -1187,6 +1206,25 @@ void tpc::ctx_sensor(tpc_ctx *c, uint32_t *width, uint32_t *height) {
 int tpc::ctx_device(tpc_ctx *c) { return c->device; }
 
 extern "C" {
+
+int tpc_bind_outputs(tpc_ctx *c, uint64_t *labels, tpc_cluster *records, size_t cap) {
+    if (!c || (labels == nullptr) != (records == nullptr) || (labels && !cap)) return TPC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->max_disorder != ~0ull) return TPC_ERR_STATE;   // one-shot steps only
+    if (labels) {   // device memory of the context's device
+        cudaPointerAttributes a{};
+        for (const void *p : {(const void *)labels, (const void *)records})
+            if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice ||
+                a.device != c->device) {
+                cudaGetLastError();
+                return TPC_ERR_ARG;
+            }
+    }
+    c->bound_labels = labels;
+    c->bound_rec = records;
+    c->bound_cap = labels ? cap : 0;
+    return TPC_OK;
+}
 
 int tpc_variant_stats_get(tpc_ctx *c, tpc_variant_stats *out) {
     if (!c || !out) return TPC_ERR_ARG;

@@ -306,3 +306,41 @@ def test_cta_cap_gives_the_same_result(cap):
     hits, _ = synth.cfg1(scale=1_500_000 / (64 * 2**20), seed=95)
     check_against_oracle(hits, 256, 256, 128, ctas_per_sm=cap)
     check_against_oracle(hits[:200_000], 256, 256, 128, "static", ctas_per_sm=cap)
+
+
+@pytest.mark.parametrize("variant", ["local", "static", "global"])
+def test_bound_outputs_written_in_place(variant):
+    """tpc_bind_outputs: the step writes labels and records straight into the
+    caller's device buffers, equal to the oracle's; retrieval still works;
+    too small a buffer refuses the step and leaves the hits pending."""
+    from paper_2412_11809_gb300 import CLUSTER_DTYPE
+    hits, _ = synth.cfg1(scale=1 / 256, seed=71)
+    n = len(hits)
+    want = oracle.labels(hits, 256, 256, 128, variant)
+    ref = oracle.features(hits, want)
+    d_lab = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    d_rec = torch.zeros((n, CLUSTER_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+    with Clusterer(256, 256, 128, variant) as c:
+        c.bind_outputs(d_lab.data_ptr(), d_rec.data_ptr(), n)
+        for rep in range(2):
+            c.push(torch.from_numpy(hits.view(np.uint8).reshape(-1, 16)).cuda())
+            c.flush()
+            _, m, _ = c.counts()
+            np.testing.assert_array_equal(d_lab.cpu().numpy().view(np.uint64) - np.uint64(rep * n), want)
+            rec = d_rec.cpu().numpy().view(CLUSTER_DTYPE).reshape(-1)[:m].copy()
+            rec["label"] -= np.uint64(rep * n)
+            assert_features_equal(rec, ref)
+            np.testing.assert_array_equal(c.labels() - np.uint64(rep * n), want)   # retrieval copies too
+        small = torch.zeros((n // 2, CLUSTER_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+        c.bind_outputs(d_lab.data_ptr(), small.data_ptr(), n // 2)
+        c.push(hits)
+        with pytest.raises(TpcError) as e:
+            c.flush()
+        assert e.value.name == "TPC_ERR_CAP"
+        c.bind_outputs(None, None)
+        c.flush()                                  # the hits were left pending
+        np.testing.assert_array_equal(c.labels() - np.uint64(2 * n), want)
+    with Clusterer(256, 256, 128) as c:
+        host = np.zeros(n, dtype=np.uint64)
+        with pytest.raises(TpcError):
+            c.bind_outputs(host.ctypes.data, host.ctypes.data, n)
