@@ -150,7 +150,10 @@ __global__ void __launch_bounds__(ACC_THREADS, ACC_SPAN >= 2048 ? 2 : 4) k_accum
                     if (want_max) atomicMax(&sl.maxkey, a_max[k]);
                 }
             }
-            __syncthreads();
+            // no barrier here: the next span re-initialises shared slot k only in
+            // the thread that has just flushed it (the same k = q * ACC_THREADS +
+            // thread mapping), before its first barrier, and no other thread
+            // touches slot k until after that barrier
         }
     }
 }

@@ -27,11 +27,10 @@
 
 namespace tpc {
 
-constexpr int LS_THREADS = 512;                // 16 warps, 8 elements each: 2 CTAs per SM
+constexpr int LS_THREADS = 256;
 constexpr int LS_WARPS = LS_THREADS / 32;
-constexpr int LS_ITEMS = TILE / LS_THREADS;    // 8
-constexpr int LS_WARP_SPAN = TILE / LS_WARPS;  // 256
-constexpr int LM_THREADS = 256;                // the border merge
+constexpr int LS_ITEMS = TILE / LS_THREADS;    // 16
+constexpr int LS_WARP_SPAN = TILE / LS_WARPS;  // 512
 constexpr uint16_t LS_NONE = 0xFFFFu;
 constexpr int LS_BITS = 9;                     // digit width of the in-tile sort
 constexpr int LS_RADIX = 1 << LS_BITS;         // 512 buckets: a 17-bit tile span in 2 passes
@@ -72,7 +71,7 @@ constexpr int LS_SMEM = (int)sizeof(LsShared);
 // every hit).  Per pass a thread
 // holds its 16 elements' local indices two to a register and each digit
 // with its rank among the warp's equal digits in one register.
-__global__ void __launch_bounds__(LS_THREADS, 2) k_tile_sort(Work w) {
+__global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
     extern __shared__ __align__(16) unsigned char ls_raw[];
     LsShared &S = *reinterpret_cast<LsShared *>(ls_raw);
     const Prob &P = *w.prob;
@@ -174,13 +173,11 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_tile_sort(Work w) {
             }
             __syncthreads();
             {   // per digit: prefix over warps; then exclusive scan of the digit totals
-                // (LS_DPT consecutive digits per thread)
-                constexpr int LS_DPT = LS_RADIX / LS_THREADS;
-                static_assert(LS_DPT >= 1 && LS_RADIX % LS_THREADS == 0, "digits per thread");
-                const uint32_t d0 = LS_DPT * threadIdx.x;
-                uint32_t tot[LS_DPT], all = 0;
+                // (LS_RADIX / LS_THREADS = 2 consecutive digits per thread)
+                const uint32_t d0 = 2 * threadIdx.x;
+                uint32_t tot2[2];
 #pragma unroll
-                for (int u = 0; u < LS_DPT; ++u) {
+                for (int u = 0; u < 2; ++u) {
                     uint32_t sum = 0;
 #pragma unroll
                     for (int q = 0; q < LS_WARPS; ++q) {
@@ -188,10 +185,10 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_tile_sort(Work w) {
                         S.wcnt[q][d0 + u] = (uint16_t)sum;
                         sum += c;
                     }
-                    tot[u] = sum;
-                    all += sum;
+                    tot2[u] = sum;
                 }
-                uint32_t x = all;
+                const uint32_t both = tot2[0] + tot2[1];
+                uint32_t x = both;
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                     if (lane >= o) x += y;
@@ -200,12 +197,8 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_tile_sort(Work w) {
                 __syncthreads();
                 uint32_t pre = 0;
                 for (int q = 0; q < warp; ++q) pre += S.warp[q];
-                uint32_t run = pre + x - all;
-#pragma unroll
-                for (int u = 0; u < LS_DPT; ++u) {
-                    S.dstart[d0 + u] = (uint16_t)run;
-                    run += tot[u];
-                }
+                S.dstart[d0] = (uint16_t)(pre + x - both);
+                S.dstart[d0 + 1] = (uint16_t)(pre + x - both + tot2[0]);
             }
             __syncthreads();
 #pragma unroll
@@ -261,7 +254,7 @@ __device__ __forceinline__ bool lm_below(uint32_t ka, uint32_t pa, uint32_t kb, 
 // pass can write every array straight to its output position.
 constexpr uint32_t MERGE_BAND = TILE / 4;
 
-__global__ void __launch_bounds__(LM_THREADS) k_tile_merge(Work w) {
+__global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
     extern __shared__ __align__(16) unsigned char lm_raw[];
     LmShared &S = *reinterpret_cast<LmShared *>(lm_raw);
     const Prob &P = *w.prob;
@@ -280,7 +273,7 @@ __global__ void __launch_bounds__(LM_THREADS) k_tile_merge(Work w) {
             const uint32_t na = band, nb = band < nb_all ? band : nb_all;
             const uint32_t a0 = begin - na;   // A = [a0, begin), B = [begin, begin + nb)
             if (threadIdx.x < 2) S.cut[threadIdx.x] = 0;
-            for (uint32_t j = threadIdx.x; j < na + nb; j += LM_THREADS) {
+            for (uint32_t j = threadIdx.x; j < na + nb; j += LS_THREADS) {
                 S.key[j] = w.keys[0][a0 + j];
                 S.pos[j] = w.vals[0][a0 + j];
             }
@@ -288,9 +281,9 @@ __global__ void __launch_bounds__(LM_THREADS) k_tile_merge(Work w) {
             {   // ia = A elements below B[0]; ib = B elements below A[last]
                 const uint32_t kb0 = S.key[na], pb0 = S.pos[na], kal = S.key[na - 1], pal = S.pos[na - 1];
                 uint32_t ca = 0, cb = 0;
-                for (uint32_t j = threadIdx.x; j < na; j += LM_THREADS)
+                for (uint32_t j = threadIdx.x; j < na; j += LS_THREADS)
                     ca += lm_below(S.key[j], S.pos[j], kb0, pb0);
-                for (uint32_t j = threadIdx.x; j < nb; j += LM_THREADS)
+                for (uint32_t j = threadIdx.x; j < nb; j += LS_THREADS)
                     cb += lm_below(S.key[na + j], S.pos[na + j], kal, pal);
                 for (int o = 16; o; o >>= 1) {
                     ca += __shfl_xor_sync(0xffffffffu, ca, o);
@@ -310,7 +303,7 @@ __global__ void __launch_bounds__(LM_THREADS) k_tile_merge(Work w) {
             }
             // moving part: A[ia, na) then B[0, ib) (indices in S); outputs a0 + ia ...
             const uint32_t ma = na - ia, m = ma + ib;
-            for (uint32_t j = threadIdx.x; j < m; j += LM_THREADS) {
+            for (uint32_t j = threadIdx.x; j < m; j += LS_THREADS) {
                 const bool in_a = j < ma;
                 const uint32_t src = in_a ? ia + j : na + (j - ma);
                 const uint32_t kk = S.key[src], pp = S.pos[src];
@@ -326,7 +319,7 @@ __global__ void __launch_bounds__(LM_THREADS) k_tile_merge(Work w) {
             }
             __syncthreads();
             const uint32_t o0 = a0 + ia;
-            for (uint32_t j = threadIdx.x; j < m; j += LM_THREADS) {
+            for (uint32_t j = threadIdx.x; j < m; j += LS_THREADS) {
                 const uint32_t src = j < ma ? ia + j : na + (j - ma);
                 const uint32_t o = o0 + S.rank[j];
                 w.keys[0][o] = S.key[src];
@@ -367,7 +360,7 @@ cudaError_t init_sortfast_attributes() {
 void launch_sort_fast(const Work &w, const Launch &L) {
     k_tile_sort<<<L.fit(k_tile_sort, LS_THREADS, LS_SMEM, G_SORT), LS_THREADS, LS_SMEM, L.stream>>>(w);
     L.mark("k_tile_sort");
-    k_tile_merge<<<L.fit(k_tile_merge, LM_THREADS, LM_SMEM, G_SORT), LM_THREADS, LM_SMEM, L.stream>>>(w);
+    k_tile_merge<<<L.fit(k_tile_merge, LS_THREADS, LM_SMEM, G_SORT), LS_THREADS, LM_SMEM, L.stream>>>(w);
     L.mark("k_tile_merge");
     k_sort_check<<<L.fit(k_sort_check, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_sort_check");
