@@ -2,9 +2,9 @@
 // t late), in three kernels, with the general LSD radix sort (radix.cu) as
 // the fallback:
 //
-//   k_tile_sort   every tile of TILE input positions is read (ToA words
-//                 first, pixels and ToTs again at output from L2) and sorted
-//                 in shared memory by a block radix sort over the key bits
+//   k_tile_sort   every tile of TILE input positions is read once, whole
+//                 records into shared memory, and sorted there by a block
+//                 radix sort over the key bits
 //                 that vary inside the tile; the sorted keys, positions,
 //                 pixels and ToTs are written out, so no separate gather is
 //                 needed.  Being the first pass over the hits, it also
@@ -54,6 +54,8 @@ __device__ __forceinline__ uint32_t ls_match_digit(uint32_t d, uint32_t vmask) {
 
 struct LsShared {
     uint32_t key[TILE];
+    uint32_t pix[TILE];          // per local input index: x | y << 16 (read once, with the ToA)
+    uint16_t tot[TILE];          // per local input index: ToT
     uint16_t idx[TILE];          // local input index of the element at each rank
     uint16_t wcnt[LS_WARPS][LS_RADIX];
     uint16_t dstart[LS_RADIX];
@@ -64,11 +66,11 @@ struct LsShared {
 
 constexpr int LS_SMEM = (int)sizeof(LsShared);
 
-// Only keys and the permutation live in shared memory; pixels and ToTs are
-// fetched again at output, in sorted order, from the tile just read (still in
-// L2), where the pixels are also checked against the sensor.  The load phase
-// also reduces the segment's ToA extremes (this pass is the first to see
-// every hit).  Per pass a thread
+// Each record is read once, whole (16-byte loads); keys, pixels, ToTs and
+// the permutation live in shared memory, and the output pass writes the
+// sorted arrays from there, checking the pixels against the sensor.  The
+// load phase also reduces the segment's ToA extremes (this pass is the
+// first to see every hit).  Per pass a thread
 // holds its 16 elements' local indices two to a register and each digit
 // with its rank among the warp's equal digits in one register.
 __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
@@ -88,20 +90,22 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
         const uint32_t new0 = g.n_carry > begin - g.off ? g.n_carry - (begin - g.off) : 0;   // first new hit
         uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
         uint64_t tmin = ~0ull, tmax = 0, cmin = ~0ull;   // ToA extremes; minimum of the new hits
-        constexpr int HALF = LS_ITEMS / 2;   // two batches of loads keep registers in bounds
+        constexpr int HALF = LS_ITEMS / 4;   // four batches of whole-record loads keep registers in bounds
 #pragma unroll
-        for (int hb = 0; hb < 2; ++hb) {
-            uint2 tv[HALF];   // ToA words of each hit
+        for (int hb = 0; hb < LS_ITEMS / HALF; ++hb) {
+            uint4 tv[HALF];   // whole records: the pixel and ToT go to shared memory for the output
 #pragma unroll
             for (int r = 0; r < HALF; ++r) {
                 const uint32_t li = (hb * HALF + r) * LS_THREADS + threadIdx.x;
-                if (li < n_t) tv[r] = __ldg(reinterpret_cast<const uint2 *>(hits + li) + 1);
+                if (li < n_t) tv[r] = ld_hit(hits + li);
             }
 #pragma unroll
             for (int r = 0; r < HALF; ++r) {
                 const uint32_t li = (hb * HALF + r) * LS_THREADS + threadIdx.x;
                 if (li < n_t) {
-                    const uint64_t toa = ((uint64_t)tv[r].y << 32) | tv[r].x;
+                    const uint64_t toa = hit_toa(tv[r]);
+                    S.pix[li] = tv[r].x;
+                    S.tot[li] = (uint16_t)hit_tot(tv[r]);
                     const uint32_t key = (uint32_t)(toa - base);
                     tmin = toa < tmin ? toa : tmin;
                     tmax = toa > tmax ? toa : tmax;
@@ -213,12 +217,12 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
         const uint32_t W = g.width, H = g.height;
         for (uint32_t j = threadIdx.x; j < n_t; j += LS_THREADS) {
             const uint32_t li = S.idx[j];
-            const uint2 px = __ldg(reinterpret_cast<const uint2 *>(hits + li));   // x | y << 16, ToT
-            bad |= (px.x & 0xFFFFu) >= W || (px.x >> 16) >= H;
+            const uint32_t px = S.pix[li];   // x | y << 16
+            bad |= (px & 0xFFFFu) >= W || (px >> 16) >= H;
             w.keys[0][begin + j] = S.key[li];
             w.vals[0][begin + j] = begin + li;
-            w.spix[begin + j] = clamp_pix(px.x, W, H);
-            w.stot[begin + j] = (uint16_t)(px.y & 0xFFFFu);
+            w.spix[begin + j] = clamp_pix(px, W, H);
+            w.stot[begin + j] = S.tot[li];
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&w.prob->err, E_RANGE);
     }
