@@ -30,7 +30,8 @@
 // the halo bucketed by cell.  Unions run on the global forest.
 //
 // k_flatten (variants (b) and (c) only): full path compression; records each
-// position's root and initialises the per-root feature slots.
+// position's root and initialises the per-root feature slots.  k_init_roots
+// (after the (b)/(c) merges): the slots of the final roots only.
 #include "tpc_internal.cuh"
 
 namespace tpc {
@@ -899,6 +900,24 @@ void launch_tile_border(const Work &w, const Launch &L) {
 void launch_flatten(const Work &w, const Launch &L) {
     k_flatten<<<L.fit(k_flatten, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_flatten");
+}
+
+// After the (b)/(c) merges: zero the feature slot of every root (parent[s]
+// == s); k_accumulate finds each position's root itself.
+__global__ void __launch_bounds__(256) k_init_roots(Work w) {
+    const uint32_t nt = w.prob->ntiles;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x)
+            if (w.parent[s] == s) init_slot(w, s);
+    }
+}
+
+void launch_init_roots(const Work &w, const Launch &L) {
+    k_init_roots<<<L.fit(k_init_roots, 256, 0), 256, 0, L.stream>>>(w);
+    L.mark("k_init_roots");
 }
 
 // Tile links and border links; roots are found by k_accumulate.

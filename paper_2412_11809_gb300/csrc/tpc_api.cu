@@ -872,7 +872,7 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
             exact = true;
         }
     }
-    launch_flatten(w, L);
+    launch_init_roots(w, L);   // parents may be deep: k_accumulate finds the roots
     launch_features(w, L);
     launch_outputs(w, L);
     if (cudaGetLastError() != cudaSuccess) return TPC_ERR_CUDA;

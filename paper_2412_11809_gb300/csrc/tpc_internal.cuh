@@ -343,6 +343,7 @@ void launch_link(const Work &w, const Launch &L);          // tile + border + fl
 void launch_tile_border(const Work &w, const Launch &L);
 int link_bands(uint32_t W, uint32_t H);   // table bands of a sensor, 0 = general link kernel
 void launch_flatten(const Work &w, const Launch &L);
+void launch_init_roots(const Work &w, const Launch &L);
 void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const Launch &L);
 Work variant_view(const Work &w, const VarWork &v);
 void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L);
