@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(ACC_THREADS, ACC_SPAN >= 2048 ? 2 : 4) k_accum
     static_assert((unsigned long long)ACC_SPAN * 0xFFFFu < (1ull << 32), "packed sum ToT fits 32 bits");
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
-    const uint32_t *sidx = w.vals[sorted_sel(P)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(P));
+    const uint32_t *sidx = pick(w.vals, sorted_sel(P));
     const int lane = threadIdx.x & 31;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(Work w) {
 __global__ void __launch_bounds__(TILE_WORDS) k_records(Work w) {
     __shared__ uint32_t s_warp[TILE_WORDS / 32];
     const uint32_t nt = w.prob->ntiles, cap = w.prob->tile_cap;
-    const uint32_t *skey = w.keys[sorted_sel(*w.prob)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(*w.prob));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];

@@ -29,9 +29,11 @@
 // staged windows when both are small; otherwise block-wide, pairwise or with
 // the halo bucketed by cell.  Unions run on the global forest.
 //
-// k_flatten (variants (b) and (c) only): full path compression; records each
-// position's root and initialises the per-root feature slots.  k_init_roots
-// (after the (b)/(c) merges): the slots of the final roots only.
+// k_sorted_roots (variants (b) and (c) only): the root of every sorted
+// position after the (a) links, into the idle radix buffer (the forest is
+// left as it is; every root is a tile root, whose slot the tile kernels
+// zeroed).  k_init_roots (after the (b)/(c) merges): the slots of the final
+// roots, which (c) can pick among non-roots.
 #include "tpc_internal.cuh"
 
 namespace tpc {
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
     static_assert(2 * NBUCKETS + 1 >= TILE + 1, "prefix array size");
 
     const Prob &P = *w.prob;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(P));
     // tiles of large sensors, then the tiles the table kernel gave back
     const uint32_t n_large = P.ntiles, n_all = P.ntiles + P.redo_count;
     for (uint32_t u = blockIdx.x; u < n_all; u += gridDim.x) {
@@ -463,7 +465,11 @@ __device__ __forceinline__ void tab_walk(TabShared &S, uint32_t k, uint32_t key,
     while (more) {   // lists holding more than one hit
         const int n = __ffs(more) - 1;
         more &= more - 1;
-        uint32_t j = S.next[hd[n]];
+        uint32_t h = hd[0];
+#pragma unroll
+        for (int m = 1; m < 9; ++m)   // a select, not an indexed load: hd stays in registers
+            if (m == n) h = hd[m];
+        uint32_t j = S.next[h];
         int steps = 1;
         for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps)
             if (j < k && key - S.key[j] <= dt) consider(j);
@@ -498,7 +504,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     volatile uint32_t *vpar = S.par;
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(P));
     const int lane = threadIdx.x & 31;
     for (uint32_t i = threadIdx.x; i < TAB_CAP / 2; i += TAB_THREADS)
         reinterpret_cast<uint32_t *>(S.tab)[i] = 0xFFFFFFFFu;
@@ -674,7 +680,7 @@ __global__ void __launch_bounds__(BF_WARPS * 32, 4) k_border_fast(Work w) {
     __shared__ uint32_t s_ne[BF_WARPS];
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(P));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *hk = s_hk[warp], *hp = s_hp[warp], *hr = s_hr[warp], *ea = s_ea[warp], *eb = s_eb[warp];
     if (lane == 0) s_ne[warp] = 0;
@@ -760,7 +766,7 @@ __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
     __shared__ uint16_t b_seg[HALO_BATCH];
     const Prob &P = *w.prob;
     const uint32_t nlist = P.border_count;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(P));
     for (uint32_t u = blockIdx.x; u < nlist; u += gridDim.x) {
         const uint32_t t = w.border_list[u];
         const Seg &g = w.seg[w.tile_seg[t]];
@@ -837,34 +843,30 @@ __global__ void __launch_bounds__(BORDER_THREADS) k_border_link(Work w) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_flatten(Work w) {
+__global__ void __launch_bounds__(256) k_sorted_roots(Work w) {
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
-    const uint32_t *sidx = w.vals[sorted_sel(P)];
-    uint32_t *sroot = w.keys[sorted_sel(P) ^ 1u];
+    uint32_t *sroot = pick(w.keys, sorted_sel(P) ^ 1u);   // the idle radix buffer
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
         tile_range(g, t, begin, end);
         constexpr int ITEMS = TILE / 256;
-        uint32_t par[ITEMS], pos[ITEMS];
+        uint32_t par[ITEMS], p2[ITEMS];
 #pragma unroll
-        for (int q = 0; q < ITEMS; ++q) {
+        for (int q = 0; q < ITEMS; ++q) {   // every load in flight before any use
             const uint32_t s = begin + q * 256 + threadIdx.x;
-            par[q] = s < end ? w.parent[s] : 0;
-            pos[q] = s < end ? sidx[s] : 0;
+            par[q] = s < end ? w.parent[s] : s;
+        }
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {   // the second hop for every item at once (most paths end there)
+            const uint32_t s = begin + q * 256 + threadIdx.x;
+            p2[q] = par[q] != s ? w.parent[par[q]] : s;
         }
 #pragma unroll
         for (int q = 0; q < ITEMS; ++q) {
             const uint32_t s = begin + q * 256 + threadIdx.x;
-            if (s >= end) continue;
-            const uint32_t r = par[q] == s ? s : gfind(w.parent, par[q]);
-            // the idle radix buffer receives each sorted position's root: only
-            // this thread writes it (parent[] itself may still be rewritten by
-            // other threads' path halving with a stale ancestor)
-            sroot[s] = r;
-            w.root_of[pos[q]] = r;
-            if (r == s) init_slot(w, r);
+            if (s < end) sroot[s] = p2[q] == par[q] ? p2[q] : gfind(w.parent, p2[q]);
         }
     }
 }
@@ -897,9 +899,9 @@ void launch_tile_border(const Work &w, const Launch &L) {
     L.mark("k_border_link");
 }
 
-void launch_flatten(const Work &w, const Launch &L) {
-    k_flatten<<<L.fit(k_flatten, 256, 0), 256, 0, L.stream>>>(w);
-    L.mark("k_flatten");
+void launch_sorted_roots(const Work &w, const Launch &L) {
+    k_sorted_roots<<<L.fit(k_sorted_roots, 256, 0), 256, 0, L.stream>>>(w);
+    L.mark("k_sorted_roots");
 }
 
 // After the (b)/(c) merges: zero the feature slot of every root (parent[s]

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_make_keys(Work w) {
 __global__ void __launch_bounds__(256) k_gather(Work w) {
     if (!w.prob->fallback) return;   // the tile sort wrote pixels and ToTs already
     const uint32_t nt = w.prob->ntiles;
-    const uint32_t *vals = w.vals[sorted_sel(*w.prob)];
+    const uint32_t *vals = pick(w.vals, sorted_sel(*w.prob));
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;

@@ -6,7 +6,7 @@
 //   setup -> tile sort -> tile merge -> sort check -> segment finalize ->
 //   (general-order fallback: keys -> radix passes 0..3 -> gather) ->
 //   table link -> tile link (redo tiles) -> border fast -> border link ->
-//   flatten -> accumulate -> labels -> tile scan -> records ->
+//   accumulate (finds the roots) -> labels -> tile scan -> records ->
 //   stream compact -> stream end.
 // Streaming contexts also checkpoint and restore their open state here
 // (tpc_snapshot / tpc_restore).
@@ -229,8 +229,8 @@ struct VarSpace {
         v.cpar = mem.alloc<uint32_t>(positions, e);
         v.glast = mem.alloc<uint32_t>(positions, e);
         v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
-        v.latest = mem.alloc<uint32_t>(9 * positions, e);
-        v.lat_stride = (uint32_t)positions;
+        v.pstate = mem.alloc<uint4>(positions, e);
+        v.tline = mem.alloc<uint4>(positions, e);
         v.changed = mem.alloc<uint32_t>(4, e);
         v.ecount = mem.alloc<unsigned long long>(2, e);
         // open (b) edges: 4 per position per list; a round that finds more
@@ -793,8 +793,9 @@ int tpc_push(tpc_ctx *c, const tpc_hit *hits, size_t n, int where) {
     return TPC_OK;
 }
 
-// Variants (b) and (c): the (a) forest first, then the variant's kernels
-// (csrc/variants.cu), then the shared flatten / feature / output kernels.
+// Variants (b) and (c): the (a) forest and its roots first, then the
+// variant's kernels (csrc/variants.cu), then the shared feature / output
+// kernels.
 // Launched without a graph; (b) waits for the host between rounds.
 static int flush_variant(tpc_ctx *c, Tracer *tr) {
     const size_t n = c->pending;
@@ -823,7 +824,7 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
     for (int pass = 0; pass < 4; ++pass) launch_radix_pass(w, pass, L);
     launch_gather(w, L);
     launch_tile_border(w, L);
-    launch_flatten(w, L);
+    launch_sorted_roots(w, L);
     const Work wv = variant_view(w, v);
     if (c->variant == TPC_STATIC) {
         launch_variant_keys(w, v, 0, L);
@@ -852,7 +853,7 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
         c->vstats_pending = false;
         for (int round = 0;; ++round) {
             if (round > 4096) return TPC_ERR_TIMEOUT;
-            launch_global_edges(w, v, full, in, L);
+            launch_global_edges(w, v, full, round == 0, in, L);   // round 0: k_sorted_roots' roots hold
             ++c->vstats.rounds;
             if (full) ++c->vstats.full_rounds;
             if (cudaMemcpyAsync(c->h_flag, v.changed, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
@@ -872,7 +873,10 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
             exact = true;
         }
     }
-    launch_init_roots(w, L);   // parents may be deep: k_accumulate finds the roots
+    // (b) only merges, so its roots are (a) roots, whose slots the tile
+    // kernels zeroed; a (c) root can be any hit.  k_accumulate finds the
+    // roots (the parents may be deep).
+    if (c->variant == TPC_STATIC) launch_init_roots(w, L);
     launch_features(w, L);
     launch_outputs(w, L);
     if (cudaGetLastError() != cudaSuccess) return TPC_ERR_CUDA;

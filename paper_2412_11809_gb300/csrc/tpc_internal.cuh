@@ -139,17 +139,17 @@ struct Work {
 // Extra arrays of the (b)/(c) variants (single-segment steps only).
 struct VarWork {
     uint32_t *k[2], *v[2];     // grouping radix sort: keys / sorted positions
-    uint32_t *cpar;            // (c): forest over the root-grouped order; (b): timeline index of each position
+    uint32_t *cpar;            // (c): forest over the root-grouped order
     uint32_t *glast;           // (b): per root, last key of its group
     uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
-    uint32_t *latest;          // (b): [9][lat_stride]: for the hit at each pixel-timeline index, the
-                               //      latest earlier hit (sorted position) on each neighbour pixel
-    uint32_t lat_stride;       // (b): entries per direction of latest
+    uint4 *pstate, *tline;     // (b): before a full round, per sorted position and per pixel-timeline
+                               //      entry: (sorted position, root of its group, the group's last key,
+                               //      its key)
     uint32_t *changed;         // (b): [0] a round merged something, [1] the edge list overflowed;
                                // (c): [0] windowed components, [1] of those swept again by a CTA,
                                //      [2] of those swept from global memory
     unsigned long long *ecount;  // (b): edges pushed to lists 0 and 1 (beyond edge_cap: overflow)
-    uint2 *edges[2];           // (b): edges (hit, latest neighbour) not merged yet, ping-pong
+    uint2 *edges[2];           // (b): edges (hit, a member of its latest neighbour's group) not merged yet
     uint32_t edge_cap;         // (b): entries each edge list holds
     uint32_t *work;            // (c): next chunk of the grouped order to sweep
     uint2 *big;                // (c): (first grouped position, hits) of components for the big window
@@ -172,6 +172,12 @@ __device__ __forceinline__ uint64_t gidx_of(const Seg &s, uint32_t local) {
 }
 
 __device__ __forceinline__ uint32_t sorted_sel(const Prob &p) { return p.npasses & 1u; }
+
+// One of a pair of buffers by a runtime bit, as a select: indexing a kernel
+// parameter's array with a runtime value would copy the parameter to local
+// memory.
+template <class T>
+__device__ __forceinline__ T *pick(T *const (&a)[2], uint32_t sel) { return sel ? a[1] : a[0]; }
 
 // Zero the feature slot of root r (a tile root; every global root is one).
 __device__ __forceinline__ void init_slot(const Work &w, uint32_t r) {
@@ -339,17 +345,17 @@ void launch_sort_fast(const Work &w, const Launch &L);
 cudaError_t init_sortfast_attributes();
 void launch_radix_pass(const Work &w, int pass, const Launch &L);
 void launch_gather(const Work &w, const Launch &L);
-void launch_link(const Work &w, const Launch &L);          // tile + border + flatten
+void launch_link(const Work &w, const Launch &L);          // tile + border links
 void launch_tile_border(const Work &w, const Launch &L);
 int link_bands(uint32_t W, uint32_t H);   // table bands of a sensor, 0 = general link kernel
-void launch_flatten(const Work &w, const Launch &L);
+void launch_sorted_roots(const Work &w, const Launch &L);
 void launch_init_roots(const Work &w, const Launch &L);
 void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const Launch &L);
 Work variant_view(const Work &w, const VarWork &v);
 void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L);
 void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, const Launch &L);
 void launch_group_last(const Work &w, const VarWork &v, const Launch &L);
-void launch_global_edges(const Work &w, const VarWork &v, int full, int in_list, const Launch &L);
+void launch_global_edges(const Work &w, const VarWork &v, int full, int flat, int in_list, const Launch &L);
 void launch_features(const Work &w, const Launch &L);
 void launch_outputs(const Work &w, const Launch &L);
 

@@ -37,7 +37,7 @@ __device__ __forceinline__ bool adjacent_v(uint32_t a, uint32_t b) {
 __global__ void __launch_bounds__(256) k_var_keys(Work w, VarWork v, int by_pixel) {
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
-    const uint32_t *sroot = w.keys[sorted_sel(P) ^ 1u];
+    const uint32_t *sroot = pick(w.keys, sorted_sel(P) ^ 1u);
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
@@ -229,10 +229,9 @@ __device__ bool sweep_windowed(WindowView<CAP> V, const uint32_t *skey, const ui
 
 __global__ void __launch_bounds__(SW_WARPS * 32) k_static_sweep(Work w, VarWork v) {
     __shared__ uint32_t s_k[SW_WARPS][SW_CAP], s_p[SW_WARPS][SW_CAP], s_c[SW_WARPS][SW_CAP];
-    const Prob &P = *w.prob;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(*w.prob));
     const uint32_t sel = v.prob->npasses & 1u;
-    const uint32_t *gk = v.k[sel], *gv = v.v[sel];
+    const uint32_t *gk = pick(v.k, sel), *gv = pick(v.v, sel);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Seg &g = w.seg[0];
     const uint32_t first = g.off, last = g.off + g.n, dt = g.dt;
@@ -335,9 +334,8 @@ __device__ void sweep_block(const SweepView<STAGED> &V, uint32_t n, uint32_t dt,
 __global__ void __launch_bounds__(BIG_THREADS) k_static_sweep_big(Work w, VarWork v) {
     extern __shared__ uint32_t big_raw[];
     __shared__ uint32_t s_min[2];
-    const Prob &P = *w.prob;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
-    const uint32_t *gv = v.v[v.prob->npasses & 1u];
+    const uint32_t *skey = pick(w.keys, sorted_sel(*w.prob));
+    const uint32_t *gv = pick(v.v, v.prob->npasses & 1u);
     const uint32_t dt = w.seg[0].dt, nbig = v.changed[1];
     for (uint32_t k = blockIdx.x; k < nbig; k += gridDim.x) {
         const uint2 job = v.big[k];
@@ -406,44 +404,31 @@ __global__ void __launch_bounds__(1024) k_pixel_scan(Work w, VarWork v) {
     }
 }
 
-// (b), once before the rounds: for every hit and each of its 9 pixels the
-// latest earlier hit there, or none.  Hits grouped by pixel (timelines, each
-// in (ToA, position) order) are taken in timeline order, a thread per hit and
-// direction, the hit's pixel from the grouping sort's keys: the latest
-// earlier hit on the neighbour pixel is found by a binary search in that
-// pixel's timeline (the lanes of a warp search the same timeline for nearby
-// values, so their probes mostly hit the same lines; the pixel itself: the
-// previous entry).  Results are stored in timeline order, latest[d * stride
-// + i] for the hit at timeline index i (coalesced); the d = 4 pass also
-// records each position's timeline index (cpar).
-__global__ void __launch_bounds__(256) k_pixel_latest(Work w, VarWork v) {
+// (b), before a full round: each hit's state, (sorted position, root of
+// its group, that group's last key, its key), first in position order
+// (coalesced but for the roots' last keys, which lie near), then gathered
+// into pixel-timeline order, one 16-byte read per hit.  The roots and last
+// keys are those of the moment (the last keys exact after k_group_last,
+// lagging later): every rule applied to them is one the sweep applies.
+// flat: right after k_sorted_roots, whose roots of the sorted positions lie in
+// the idle radix buffer (the forest itself may still be deeper); the last
+// keys are kept at roots only.
+__global__ void __launch_bounds__(256) k_position_state(Work w, VarWork v, int flat) {
     const Seg &g = w.seg[0];
-    const uint32_t W = g.width, H = g.height, n = g.n;
-    const uint32_t sel = v.prob->npasses & 1u;
-    const uint32_t *tl = v.v[sel] + g.off;   // sorted positions grouped by pixel
-    const uint32_t *tk = v.k[sel] + g.off;   // their pixel ids
-    const uint32_t *ps = v.pix_start;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t d = 0; d < 9; ++d)   // 9 n can exceed 32 bits: directions outside
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t s = tl[i], p = tk[i];
-        const int x = (int)(p % W) + (int)(d % 3) - 1, y = (int)(p / W) + (int)(d / 3) - 1;
-        uint32_t L = 0xFFFFFFFFu;
-        if (d == 4) {
-            if (i > ps[p]) L = tl[i - 1];
-            v.cpar[s] = i;   // timeline index of each position
-        } else if (x >= 0 && x < (int)W && y >= 0 && y < (int)H) {
-            const uint32_t q = (uint32_t)y * W + (uint32_t)x;
-            const uint32_t q0 = ps[q];
-            uint32_t a = q0, b = ps[q + 1];   // first entry of q's timeline at or after s
-            while (a < b) {
-                const uint32_t mid = (a + b) >> 1;
-                if (tl[mid] < s) a = mid + 1; else b = mid;
-            }
-            if (a > q0) L = tl[a - 1];
-        }
-        v.latest[(size_t)d * v.lat_stride + i] = L;
+    const uint32_t *skey = pick(w.keys, sorted_sel(*w.prob));
+    const uint32_t *sroot = pick(w.keys, sorted_sel(*w.prob) ^ 1u);
+    for (uint32_t s = g.off + blockIdx.x * blockDim.x + threadIdx.x; s < g.off + g.n; s += gridDim.x * blockDim.x) {
+        const uint32_t r = flat ? sroot[s] : gfind(w.parent, s);
+        v.pstate[s] = make_uint4(s, r, v.glast[r], skey[s]);
     }
+}
+
+__global__ void __launch_bounds__(256) k_timeline_state(Work w, VarWork v) {
+    const Seg &g = w.seg[0];
+    const uint32_t *tl = pick(v.v, v.prob->npasses & 1u) + g.off;
+    uint4 *T = v.tline + g.off;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < g.n; j += gridDim.x * blockDim.x)
+        T[j] = v.pstate[tl[j]];
 }
 
 __global__ void __launch_bounds__(256) k_group_last_reset(Work w, VarWork v) {
@@ -463,7 +448,7 @@ __global__ void __launch_bounds__(256) k_group_last_reset(Work w, VarWork v) {
 __global__ void __launch_bounds__(256) k_group_last(Work w, VarWork v) {
     const Prob &P = *w.prob;
     const uint32_t nt = P.ntiles;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(P));
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
         uint32_t begin, end;
@@ -480,16 +465,16 @@ __global__ void __launch_bounds__(256) k_group_last(Work w, VarWork v) {
 // lag behind its group's (a concurrent hook of a loses it), never exceed it,
 // so every union made on it is one the sweep makes; an exact recomputation
 // when a round merges nothing decides the end.
-__device__ __forceinline__ void gunion_last(uint32_t *parent, uint32_t *glast, uint32_t a, uint32_t b) {
+__device__ __forceinline__ bool gunion_last(uint32_t *parent, uint32_t *glast, uint32_t a, uint32_t b) {
     while (true) {
         a = gfind(parent, a);
         b = gfind(parent, b);
-        if (a == b) return;
+        if (a == b) return false;
         if (a > b) { const uint32_t t = a; a = b; b = t; }
         if (atomicCAS(parent + b, b, a) == b) {
             const uint32_t lb = *reinterpret_cast<volatile uint32_t *>(&glast[b]);
             if (*reinterpret_cast<volatile uint32_t *>(&glast[a]) < lb) atomicMax(&glast[a], lb);
-            return;
+            return true;
         }
     }
 }
@@ -516,6 +501,7 @@ __device__ __forceinline__ int global_edge(const Work &w, const VarWork &v, uint
 // Append the warp's open edges to list `out` (one atomic per warp); on
 // overflow the list is marked and the next round takes every hit again.
 __device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep, uint32_t s, uint32_t l) {
+    uint2 *list = pick(v.edges, out);
     const uint32_t m = __ballot_sync(0xffffffffu, keep);
     if (!m) return;
     const int lane = threadIdx.x & 31;
@@ -524,35 +510,130 @@ __device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep,
     base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
     const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
     if (keep) {
-        if (slot < v.edge_cap) v.edges[out][slot] = make_uint2(s, l);
+        if (slot < v.edge_cap) list[slot] = make_uint2(s, l);
         else v.changed[1] = 1u;
     }
 }
 
+// The latest entry of timeline [q0, q1) (ascending positions) before
+// position s, for the 32 lanes of a warp whose positions ascend with the
+// lane index: a 32-way search for lane 0's, then a window of the 32 entries
+// from the one before it, each lane's answer in it by five shuffles; a lane
+// whose answer lies past the window searches the rest alone.  All lanes
+// call it with the same q0, q1.
+__device__ __forceinline__ void lane_latest(const uint32_t *tl, const uint4 *T, uint32_t a, uint32_t b,
+                                            uint32_t s, uint4 &nb, bool &has) {
+    const uint32_t a0 = a;
+    while (a < b) {   // first entry of [a, b) at or after s
+        const uint32_t mid = (a + b) >> 1;
+        if (tl[mid] < s) a = mid + 1; else b = mid;
+    }
+    if (a > a0) {
+        nb = T[a - 1];
+        has = true;
+    }
+}
+
+__device__ __forceinline__ void warp_latest(const uint32_t *tl, const uint4 *T, uint32_t q0, uint32_t q1,
+                                            uint32_t s, int lane, uint4 &nb, bool &has) {
+    const uint32_t s0 = __shfl_sync(0xffffffffu, s, 0);
+    uint32_t lo = q0, hi = q1;   // the first entry at or after s0 lies in [lo, hi] (hi = q1: none)
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) >> 5, idx = lo + (uint32_t)lane * step;
+        const int c = __popc(__ballot_sync(0xffffffffu, idx < hi && tl[idx] < s0));   // a prefix of the lanes
+        if (c == 0) { hi = lo; break; }
+        const uint32_t below = lo + (uint32_t)(c - 1) * step;
+        lo = below + 1;
+        hi = min(below + step, hi);
+    }
+    if (hi > lo) lo += __popc(__ballot_sync(0xffffffffu, lo + lane < hi && tl[lo + lane] < s0));
+    // window lane j holds entry lo - 1 + j (lane 0: none if lo = q0; past q1: +inf)
+    const bool in = (lane > 0 || lo > q0) && lo + lane - 1 < q1;
+    const uint4 e = in ? T[lo + lane - 1] : make_uint4(0, 0, 0, 0);
+    const uint32_t wpos = in ? e.x : 0xFFFFFFFFu;   // lane 0's is never compared
+    int c = 0;   // entries of lanes 1..31 before s
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1)
+        if (__shfl_sync(0xffffffffu, wpos, c + st) < s) c += st;
+    nb.x = __shfl_sync(0xffffffffu, e.x, c);
+    nb.y = __shfl_sync(0xffffffffu, e.y, c);
+    nb.z = __shfl_sync(0xffffffffu, e.z, c);
+    nb.w = __shfl_sync(0xffffffffu, e.w, c);
+    has = c > 0 || lo > q0;
+    if (c == 31 && lo + 31 < q1) lane_latest(tl, T, lo + 31, q1, s, nb, has);
+}
+
 // A round over every hit's 9 latest neighbours (the first round, and any
-// round after an overflow), in (ToA, position) order, so that the forest
-// and key accesses of neighbouring threads are close and the open edges are
-// listed in time order: merges what the rule allows, lists the rest.  The
-// hit's timeline index (cpar, written by k_pixel_latest) locates its 9
-// entries.
-__global__ void __launch_bounds__(256) k_global_full(Work w, VarWork v, int out) {
-    const Prob &P = *w.prob;
+// round after an overflow of the edge list), in pixel-timeline order: a warp
+// takes 32 consecutive entries, which mostly share a pixel, and finds their
+// latest earlier entries on each neighbour pixel together (warp_latest;
+// lane by lane where the warp straddles pixels), with their state from the
+// snapshot: the snapshot root starts the find of the neighbour's group (one
+// step shorter than from the hit), its last key decides most rules without
+// a read.  Merges what the rule allows and lists the rest, as (hit, root of
+// the neighbour's group).
+__global__ void __launch_bounds__(256) k_global_first(Work w, VarWork v, int out) {
     const Seg &g = w.seg[0];
-    const uint32_t *skey = w.keys[sorted_sel(P)];
-    const uint32_t n = g.n, dt = g.dt;
+    const uint32_t W = g.width, H = g.height, n = g.n, dt = g.dt;
+    const uint32_t sel = v.prob->npasses & 1u;
+    const uint32_t *tl = pick(v.v, sel) + g.off;   // sorted positions grouped by pixel
+    const uint32_t *tk = pick(v.k, sel) + g.off;   // their pixel ids
+    const uint4 *T = v.tline + g.off;
+    const uint32_t *ps = v.pix_start;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
     bool changed = false;
-    for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {   // whole warps: ballots
-        const bool valid = i0 + threadIdx.x < n;
-        const uint32_t s = g.off + i0 + threadIdx.x;
-        const uint32_t i = valid ? v.cpar[s] : 0, ks = valid ? skey[s] : 0;
-        uint32_t rh = valid ? gfind(w.parent, s) : 0;
+    for (uint32_t i0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32u; i0 < n; i0 += warps * 32u) {
+        const uint32_t i = i0 + (uint32_t)lane;
+        const bool valid = i < n;
+        const uint4 me = valid ? T[i] : make_uint4(0, 0, 0, 0);   // position, root, last, key
+        const uint32_t p = valid ? tk[i] : 0xFFFFFFFFu;
+        const uint32_t p0 = __shfl_sync(0xffffffffu, p, 0);
+        const bool uniform = __all_sync(0xffffffffu, p == p0);
+        const int px = (int)(p % W), py = (int)(p / W);
+        uint32_t rh = me.y;   // a node of h's group, moved towards its root as the round goes
 #pragma unroll 1
         for (int d = 0; d < 9; ++d) {
-            const uint32_t l = valid ? v.latest[(size_t)d * v.lat_stride + i] : 0xFFFFFFFFu;
+            uint4 nb = make_uint4(0, 0, 0, 0);
+            bool has = false;
+            const int x = px + d % 3 - 1, y = py + d / 3 - 1;
+            const bool inside = valid && x >= 0 && x < (int)W && y >= 0 && y < (int)H;
+            if (d == 4) {
+                if (valid && i > ps[p]) {
+                    nb = T[i - 1];
+                    has = true;
+                }
+            } else if (uniform) {   // inside is the same for every lane
+                if (inside) {
+                    const uint32_t q = (uint32_t)y * W + (uint32_t)x;
+                    warp_latest(tl, T, ps[q], ps[q + 1], me.x, lane, nb, has);
+                }
+            } else if (inside) {
+                const uint32_t q = (uint32_t)y * W + (uint32_t)x;
+                lane_latest(tl, T, ps[q], ps[q + 1], me.x, nb, has);
+            }
+            // Any two nodes found equal are in one group (groups only
+            // merge), so stale roots only cost a find; the last keys used
+            // are lower bounds of the group's (nb.z: its part at the
+            // snapshot), so the rule never merges more than the sweep.
             int r = 0;
-            if (l != 0xFFFFFFFFu) r = global_edge(w, v, ks, dt, s, rh, l);
+            uint32_t rl = nb.y;
+            if (has && rl != rh) {
+                rl = gfind(w.parent, rl);
+                if (rl != rh) rh = gfind(w.parent, rh);   // h's group may have been hooked since
+                if (rl != rh) {
+                    bool ok = (uint64_t)me.w <= (uint64_t)nb.z + dt;
+                    if (!ok) ok = (uint64_t)me.w <= (uint64_t)*reinterpret_cast<volatile uint32_t *>(&v.glast[rl]) + dt;
+                    if (ok) {
+                        if (gunion_last(w.parent, v.glast, rh, rl)) r = 1;
+                        rh = min(rh, rl);
+                    } else {
+                        r = 2;
+                    }
+                }
+            }
             changed |= r == 1;
-            push_edges(v, out, r == 2, s, l);
+            push_edges(v, out, r == 2, me.x, rl);
         }
     }
     if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&v.changed[0], 1u);
@@ -560,8 +641,8 @@ __global__ void __launch_bounds__(256) k_global_full(Work w, VarWork v, int out)
 
 // A round over the open edges of list `in` only.
 __global__ void __launch_bounds__(256) k_global_list(Work w, VarWork v, int in) {
-    const Prob &P = *w.prob;
-    const uint32_t *skey = w.keys[sorted_sel(P)];
+    const uint32_t *skey = pick(w.keys, sorted_sel(*w.prob));
+    const uint2 *list = pick(v.edges, in);
     const uint32_t dt = w.seg[0].dt;
     const unsigned long long n = v.ecount[in];
     const uint32_t cnt = n < v.edge_cap ? (uint32_t)n : v.edge_cap;
@@ -570,7 +651,7 @@ __global__ void __launch_bounds__(256) k_global_list(Work w, VarWork v, int in) 
     for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < cnt; e0 += stride) {
         const uint32_t e = e0 + threadIdx.x;
         const bool valid = e < cnt;
-        const uint2 ed = valid ? v.edges[in][e] : make_uint2(0, 0);
+        const uint2 ed = valid ? list[e] : make_uint2(0, 0);
         int r = 0;
         if (valid) {
             uint32_t rh = gfind(w.parent, ed.x);
@@ -590,13 +671,16 @@ void launch_group_last(const Work &w, const VarWork &v, const Launch &L) {
 
 // One round: list `1 - in` (or, if full, every hit) into list `in`'s
 // partner.  full: out = list 0 after reading every hit.
-void launch_global_edges(const Work &w, const VarWork &v, int full, int in, const Launch &L) {
+void launch_global_edges(const Work &w, const VarWork &v, int full, int flat, int in, const Launch &L) {
     const int out = full ? 0 : 1 - in;
     cudaMemsetAsync(v.changed, 0, 2 * sizeof(uint32_t), L.stream);
     cudaMemsetAsync(v.ecount + out, 0, sizeof(unsigned long long), L.stream);
     if (full) {
-        k_global_full<<<L.fit(k_global_full, 256, 0), 256, 0, L.stream>>>(w, v, out);
-        L.mark("k_global_full");
+        k_position_state<<<L.fit(k_position_state, 256, 0), 256, 0, L.stream>>>(w, v, flat);
+        k_timeline_state<<<L.fit(k_timeline_state, 256, 0), 256, 0, L.stream>>>(w, v);
+        L.mark("k_timeline_state");
+        k_global_first<<<L.fit(k_global_first, 256, 0), 256, 0, L.stream>>>(w, v, out);
+        L.mark("k_global_first");
     } else {
         k_global_list<<<L.fit(k_global_list, 256, 0), 256, 0, L.stream>>>(w, v, in);
         L.mark("k_global_list");
@@ -632,8 +716,6 @@ void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, c
     k_pixel_hist<<<L.fit(k_pixel_hist, 256, 0), 256, 0, L.stream>>>(w, v);
     k_pixel_scan<<<1, 1024, 0, L.stream>>>(w, v);
     L.mark("k_pixel_hist_scan");
-    k_pixel_latest<<<L.fit(k_pixel_latest, 256, 0), 256, 0, L.stream>>>(w, v);
-    L.mark("k_pixel_latest");
 }
 
 
