@@ -273,7 +273,8 @@ int tpc_forest(tpc_ctx *ctx, uint32_t *parent, uint32_t *input_pos, size_t cap, 
 /* Diagnostics of the context's last TPC_GLOBAL or TPC_STATIC flush (zero
    otherwise): (b) rounds of merges on the device, of which full passes over
    every hit (the first, and any after the list of open edges overflowed),
-   and exact recomputations of the groups' last ToA; (c) components longer
+   exact recomputations of the groups' last ToA, and the edges the first
+   round left open (capped at the list's size); (c) components longer
    than a warp's shared-memory staging (512 hits), swept by one warp
    through a sliding window of 512 hits; of those, the ones swept again by a
    whole CTA (more hits within dt than that window holds), and of those the
@@ -282,6 +283,7 @@ int tpc_forest(tpc_ctx *ctx, uint32_t *parent, uint32_t *input_pos, size_t cap, 
 typedef struct tpc_variant_stats {
     uint32_t rounds, full_rounds, exact_checks;
     uint32_t windowed, window_fallbacks, global_sweeps;
+    uint32_t first_open_edges;
 } tpc_variant_stats;
 int tpc_variant_stats_get(tpc_ctx *ctx, tpc_variant_stats *out);
 

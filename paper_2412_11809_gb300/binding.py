@@ -335,10 +335,10 @@ class Clusterer:
 
     def variant_stats(self) -> dict:
         """``tpc_variant_stats_get``: diagnostics of the last (b)/(c) flush."""
-        st = (ctypes.c_uint32 * 6)()
+        st = (ctypes.c_uint32 * 7)()
         _check(self._lib.tpc_variant_stats_get(self._h, st), "tpc_variant_stats_get")
         return dict(zip(("rounds", "full_rounds", "exact_checks", "windowed", "window_fallbacks",
-                         "global_sweeps"), st))
+                         "global_sweeps", "first_open_edges"), st))
 
     def device_bytes(self) -> int:
         b = ctypes.c_size_t()

@@ -213,34 +213,51 @@ struct Workspace {
     }
 };
 
-// Arrays of the (b)/(c) variants, allocated on first use.
+// Arrays of the (b)/(c) variants, allocated on first use: the grouping
+// sort's for both, then each variant's own.
 struct VarSpace {
     VarWork v{};
     DevMem mem;
     size_t pos_cap = 0, pixels = 0;
-    cudaError_t ensure(size_t positions, size_t npixels) {
+    cudaError_t ensure(size_t positions, size_t npixels, bool global) {
         if (v.k[0] && positions <= pos_cap && npixels <= pixels) return cudaSuccess;
         mem.release();
+        v = VarWork{};
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < 2; ++i) {
             v.k[i] = mem.alloc<uint32_t>(positions, e);
             v.v[i] = mem.alloc<uint32_t>(positions, e);
         }
-        v.cpar = mem.alloc<uint32_t>(positions, e);
-        v.glast = mem.alloc<uint32_t>(positions, e);
-        v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
-        v.pstate = mem.alloc<uint4>(positions, e);
-        v.tline = mem.alloc<uint4>(positions, e);
         v.changed = mem.alloc<uint32_t>(4, e);
-        v.ecount = mem.alloc<unsigned long long>(2, e);
-        // open (b) edges: 4 per position per list; a round that finds more
-        // marks the overflow and the next round reads every hit's 9 again
-        v.edge_cap = (uint32_t)std::min<size_t>(4 * positions, 0xFFFFFFFFull);
-        v.edges[0] = mem.alloc<uint2>(v.edge_cap, e);
-        v.edges[1] = mem.alloc<uint2>(v.edge_cap, e);
-        v.work = mem.alloc<uint32_t>(1, e);
-        v.big = mem.alloc<uint2>(positions / 512 + 1, e);   // components of more than 512 hits
         v.prob = mem.alloc<Prob>(1, e);
+        if (global) {
+            const size_t tiles = positions / TILE + 2;
+            v.pix_start = mem.alloc<uint32_t>(npixels + 1, e);
+            v.tcnt = mem.alloc<uint32_t>(tiles, e);
+            v.tbase = mem.alloc<uint32_t>(tiles, e);
+            v.ncomp = mem.alloc<uint32_t>(1, e);
+            v.cid_at = mem.alloc<uint32_t>(positions, e);
+            v.croot = mem.alloc<uint32_t>(positions, e);
+            v.cpar_d = mem.alloc<uint32_t>(positions, e);
+            v.clast0 = mem.alloc<uint32_t>(positions, e);
+            v.clast = mem.alloc<uint32_t>(positions, e);
+            v.pstate = mem.alloc<uint4>(positions, e);
+            v.tline = mem.alloc<uint4>(positions, e);
+            v.ecount = mem.alloc<unsigned long long>(2, e);
+            // open edges: 2 per position per list (the first round of the
+            // 2.5 Ghits/s Timepix4 stream leaves 0.64 per hit open, later
+            // rounds fewer); a round that finds more marks the overflow and
+            // the next round reads every hit's 9 again
+            v.edge_cap = (uint32_t)std::min<size_t>(2 * positions, 0xFFFFFFFFull);
+            for (int i = 0; i < 2; ++i) {
+                v.edges[i] = mem.alloc<uint2>(v.edge_cap, e);
+                v.ekey[i] = mem.alloc<uint32_t>(v.edge_cap, e);
+            }
+        } else {
+            v.cpar = mem.alloc<uint32_t>(positions, e);
+            v.work = mem.alloc<uint32_t>(1, e);
+            v.big = mem.alloc<uint2>(positions / 512 + 1, e);   // components of more than 512 hits
+        }
         if (e != cudaSuccess) {
             mem.release();
             v = VarWork{};
@@ -306,7 +323,7 @@ struct tpc_ctx {
 
     Workspace ws;
     VarSpace vs;                   // variants (b), (c)
-    uint32_t *h_flag = nullptr;    // pinned: (b) round result
+    uint32_t *h_flag = nullptr;    // pinned: (b) round result ([0..1]) and list size ([2..3]); (c) counters
     DevMem outmem;                 // output buffers
     uint64_t *d_labels = nullptr, *d_index = nullptr;
     tpc_cluster *d_rec = nullptr;
@@ -802,9 +819,10 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
     c->has_result = false;   // the workspace may move: the last result is gone
     if (c->bound_labels && n > c->bound_cap) return TPC_ERR_CAP;
     if (c->ws.ensure(n) != cudaSuccess) return TPC_ERR_NOMEM;
-    if (c->vs.ensure(c->ws.pos_cap, (size_t)c->width * c->height) != cudaSuccess) return TPC_ERR_NOMEM;
+    if (c->vs.ensure(c->ws.pos_cap, (size_t)c->width * c->height, c->variant == TPC_GLOBAL) != cudaSuccess)
+        return TPC_ERR_NOMEM;
     if (!c->bound_labels && ensure_out(c, n) != cudaSuccess) return TPC_ERR_NOMEM;
-    if (!c->h_flag && host_alloc(&c->fail_alloc, (void **)&c->h_flag, 4 * sizeof(uint32_t)) != cudaSuccess)
+    if (!c->h_flag && host_alloc(&c->fail_alloc, (void **)&c->h_flag, 8 * sizeof(uint32_t)) != cudaSuccess)
         return TPC_ERR_NOMEM;
     Seg s = base_seg(c);
     s.hits = c->zc ? c->zc : c->in;
@@ -839,14 +857,15 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
         launch_variant_keys(w, v, 1, L);
         for (int pass = 0; pass < 3; ++pass) launch_radix_pass(wv, pass, L);
         launch_pixel_timelines(w, v, c->width * c->height, L);
-        // Rounds of the rule until the partition is closed under it: the
-        // first over every hit's 9 latest neighbours, the later ones over the
-        // edges left open (all hits again after an overflow of the list);
-        // the groups' last keys are exact at the start and kept at the roots
-        // by the unions (never above the exact value), and recomputed exactly
-        // when a round merges nothing: the end is a round without merges on
-        // exact values.
-        launch_group_last(w, v, L);
+        // Rounds of the rule until the partition is closed under it, on the
+        // (a) components' dense ids: the first over every hit's 9 latest
+        // neighbours, the later ones over the edges left open (all hits
+        // again after an overflow of the list); the groups' last keys are
+        // exact at the start (each group one component) and kept at the
+        // roots by the unions (never above the exact value), and recomputed
+        // exactly when a round merges nothing: the end is a round without
+        // merges on exact values.
+        launch_components(w, v, L);
         bool full = true, exact = true;
         int in = 0;
         c->vstats = tpc_variant_stats{};
@@ -858,8 +877,14 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
             if (full) ++c->vstats.full_rounds;
             if (cudaMemcpyAsync(c->h_flag, v.changed, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
                     cudaSuccess ||
+                (round == 0 && cudaMemcpyAsync(c->h_flag + 2, v.ecount, sizeof(unsigned long long),
+                                               cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) ||
                 cudaStreamSynchronize(c->stream) != cudaSuccess)
                 return TPC_ERR_CUDA;
+            if (round == 0) {
+                const unsigned long long listed = *reinterpret_cast<unsigned long long *>(c->h_flag + 2);
+                c->vstats.first_open_edges = (uint32_t)std::min<unsigned long long>(listed, v.edge_cap);
+            }
             const bool merged = c->h_flag[0] != 0, overflow = c->h_flag[1] != 0;
             in = full ? 0 : 1 - in;   // the list just written
             full = overflow;
@@ -868,10 +893,11 @@ static int flush_variant(tpc_ctx *c, Tracer *tr) {
                 continue;
             }
             if (exact) break;
-            launch_group_last(w, v, L);
+            launch_group_last(v, L);
             ++c->vstats.exact_checks;
             exact = true;
         }
+        launch_comp_parents(w, v, L);
     }
     // (b) only merges, so its roots are (a) roots, whose slots the tile
     // kernels zeroed; a (c) root can be any hit.  k_accumulate finds the

@@ -140,16 +140,22 @@ struct Work {
 struct VarWork {
     uint32_t *k[2], *v[2];     // grouping radix sort: keys / sorted positions
     uint32_t *cpar;            // (c): forest over the root-grouped order
-    uint32_t *glast;           // (b): per root, last key of its group
     uint32_t *pix_start;       // (b): per pixel, start of its timeline (W*H + 1)
+    uint32_t *tcnt, *tbase;    // (b): (a) components per tile and their exclusive prefix
+    uint32_t *ncomp;           // (b): number of (a) components (dense ids 0 .. ncomp - 1)
+    uint32_t *cid_at;          // (b): per sorted position that is an (a) root: its dense id
+    uint32_t *croot;           // (b): per dense id: the root's sorted position
+    uint32_t *cpar_d;          // (b): forest over dense ids (a group's root: its smallest id)
+    uint32_t *clast0, *clast;  // (b): per dense id: its component's last key; at a group's root, the group's
     uint4 *pstate, *tline;     // (b): before a full round, per sorted position and per pixel-timeline
-                               //      entry: (sorted position, root of its group, the group's last key,
-                               //      its key)
+                               //      entry: (sorted position, id of its group's root, the group's last
+                               //      key, its key)
     uint32_t *changed;         // (b): [0] a round merged something, [1] the edge list overflowed;
                                // (c): [0] windowed components, [1] of those swept again by a CTA,
                                //      [2] of those swept from global memory
     unsigned long long *ecount;  // (b): edges pushed to lists 0 and 1 (beyond edge_cap: overflow)
-    uint2 *edges[2];           // (b): edges (hit, a member of its latest neighbour's group) not merged yet
+    uint2 *edges[2];           // (b): edges not merged yet (an id of h's group, an id of its neighbour's)
+    uint32_t *ekey[2];         // (b): h's key of each edge
     uint32_t edge_cap;         // (b): entries each edge list holds
     uint32_t *work;            // (c): next chunk of the grouped order to sweep
     uint2 *big;                // (c): (first grouped position, hits) of components for the big window
@@ -354,7 +360,9 @@ void launch_variant_keys(const Work &w, const VarWork &v, int by_pixel, const La
 Work variant_view(const Work &w, const VarWork &v);
 void launch_static_sweep(const Work &w, const VarWork &v, const Launch &L);
 void launch_pixel_timelines(const Work &w, const VarWork &v, uint32_t npixels, const Launch &L);
-void launch_group_last(const Work &w, const VarWork &v, const Launch &L);
+void launch_components(const Work &w, const VarWork &v, const Launch &L);
+void launch_group_last(const VarWork &v, const Launch &L);
+void launch_comp_parents(const Work &w, const VarWork &v, const Launch &L);
 void launch_global_edges(const Work &w, const VarWork &v, int full, int flat, int in_list, const Launch &L);
 void launch_features(const Work &w, const Launch &L);
 void launch_outputs(const Work &w, const Launch &L);

@@ -21,8 +21,9 @@
 // later ones to the edges still open, with the groups' last ToA kept at the
 // roots by the unions (a lagging value only postpones a merge) and
 // recomputed exactly when a round merges nothing; the partition is final
-// after a round without merges on exact values.
-// Per-pixel timelines come from a stable radix sort of the hits by pixel.
+// after a round without merges on exact values.  The rounds join (a)
+// components, each by a dense id; per-pixel timelines come from a stable
+// radix sort of the hits by pixel.
 #include "tpc_internal.cuh"
 
 namespace tpc {
@@ -404,22 +405,143 @@ __global__ void __launch_bounds__(1024) k_pixel_scan(Work w, VarWork v) {
     }
 }
 
-// (b), before a full round: each hit's state, (sorted position, root of
-// its group, that group's last key, its key), first in position order
-// (coalesced but for the roots' last keys, which lie near), then gathered
-// into pixel-timeline order, one 16-byte read per hit.  The roots and last
-// keys are those of the moment (the last keys exact after k_group_last,
-// lagging later): every rule applied to them is one the sweep applies.
-// flat: right after k_sorted_roots, whose roots of the sorted positions lie in
-// the idle radix buffer (the forest itself may still be deeper); the last
-// keys are kept at roots only.
+// (b) takes the (a) components as its units: they get dense ids in the
+// order of their roots (sorted positions), and the rounds find and join on
+// a forest over those ids (cpar_d, with each group's last key at its root
+// in clast), a tenth of the hits' count, mostly held in L2, instead of on
+// the forest over sorted positions.  A component's own last key (clast0)
+// is fixed.  The roots of the sorted positions after the (a) links are
+// those k_sorted_roots left in the idle radix buffer.
+
+// Components per tile: the roots among its positions.
+__global__ void __launch_bounds__(256) k_comp_count(Work w, VarWork v) {
+    __shared__ uint32_t s_cnt;
+    const uint32_t nt = w.prob->ntiles;
+    const uint32_t *sroot = pick(w.keys, sorted_sel(*w.prob) ^ 1u);
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        uint32_t c = 0;
+        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) c += sroot[s] == s ? 1u : 0u;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s_cnt, c);
+        __syncthreads();
+        if (threadIdx.x == 0) v.tcnt[t] = s_cnt;
+        __syncthreads();   // s_cnt is reset for the next tile
+    }
+}
+
+// One CTA: exclusive scan of the tile counts; the total is the id count.
+__global__ void __launch_bounds__(1024) k_comp_scan(Work w, VarWork v) {
+    __shared__ uint32_t s_warp[32];
+    const uint32_t nt = w.prob->ntiles;
+    const uint32_t per = (nt + blockDim.x - 1) / blockDim.x;
+    const uint32_t i0 = threadIdx.x * per;
+    uint32_t local = 0;
+    for (uint32_t i = i0; i < i0 + per && i < nt; ++i) local += v.tcnt[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t run = x - local;
+    for (int q = 0; q < warp; ++q) run += s_warp[q];
+    for (uint32_t i = i0; i < i0 + per && i < nt; ++i) {
+        v.tbase[i] = run;
+        run += v.tcnt[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) *v.ncomp = run;
+}
+
+// Dense ids in root order: a root's id is the roots before it.  Each id
+// starts as its own group.
+__global__ void __launch_bounds__(256) k_comp_ids(Work w, VarWork v) {
+    constexpr int ITEMS = TILE / 256;
+    __shared__ uint32_t s_pre[TILE / 32];   // roots per 32 positions, then their exclusive prefix
+    const uint32_t nt = w.prob->ntiles;
+    const uint32_t *sroot = pick(w.keys, sorted_sel(*w.prob) ^ 1u);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Seg &g = w.seg[w.tile_seg[t]];
+        uint32_t begin, end;
+        tile_range(g, t, begin, end);
+        uint32_t m[ITEMS];
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {   // position begin + q * 256 + threadIdx.x: word q * 8 + warp
+            const uint32_t s = begin + q * 256 + threadIdx.x;
+            m[q] = __ballot_sync(0xffffffffu, s < end && sroot[s] == s);
+            if (lane == 0) s_pre[q * 8 + warp] = __popc(m[q]);
+        }
+        __syncthreads();
+        if (warp == 0) {   // 128 words, 4 per lane
+            uint32_t c[4], sum = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { c[k] = s_pre[lane * 4 + k]; sum += c[k]; }
+            uint32_t x = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            uint32_t run = x - sum;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { s_pre[lane * 4 + k] = run; run += c[k]; }
+        }
+        __syncthreads();
+        const uint32_t base = v.tbase[t];
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            if (!((m[q] >> lane) & 1u)) continue;
+            const uint32_t s = begin + q * 256 + threadIdx.x;
+            const uint32_t c = base + s_pre[q * 8 + warp] + __popc(m[q] & ((1u << lane) - 1u));
+            v.cid_at[s] = c;
+            v.croot[c] = s;
+            v.cpar_d[c] = c;
+            v.clast0[c] = 0;
+        }
+        __syncthreads();   // s_pre is rewritten for the next tile
+    }
+}
+
+// Each component's last key; only hits that could raise the stored value
+// issue the atomic (a long component would serialise on one address).
+__global__ void __launch_bounds__(256) k_comp_last(Work w, VarWork v) {
+    const Seg &g = w.seg[0];
+    const uint32_t *skey = pick(w.keys, sorted_sel(*w.prob));
+    const uint32_t *sroot = pick(w.keys, sorted_sel(*w.prob) ^ 1u);
+    for (uint32_t s = g.off + blockIdx.x * blockDim.x + threadIdx.x; s < g.off + g.n; s += gridDim.x * blockDim.x) {
+        const uint32_t c = v.cid_at[sroot[s]], k = skey[s];
+        if (*reinterpret_cast<volatile uint32_t *>(&v.clast0[c]) < k) atomicMax(&v.clast0[c], k);
+    }
+}
+
+// Before a full round: each hit's state, (sorted position, id of its
+// group's root, that group's last key, its key), first in position order
+// (coalesced but for the ids, whose roots lie near), then gathered into
+// pixel-timeline order, one 16-byte read per hit.  The groups and last keys
+// are those of the moment (the last keys exact at the first round, lagging
+// later): every rule applied to them is one the sweep applies.  flat: the
+// first round, where every group is one component (and starts here).
 __global__ void __launch_bounds__(256) k_position_state(Work w, VarWork v, int flat) {
     const Seg &g = w.seg[0];
     const uint32_t *skey = pick(w.keys, sorted_sel(*w.prob));
     const uint32_t *sroot = pick(w.keys, sorted_sel(*w.prob) ^ 1u);
     for (uint32_t s = g.off + blockIdx.x * blockDim.x + threadIdx.x; s < g.off + g.n; s += gridDim.x * blockDim.x) {
-        const uint32_t r = flat ? sroot[s] : gfind(w.parent, s);
-        v.pstate[s] = make_uint4(s, r, v.glast[r], skey[s]);
+        const uint32_t r = sroot[s], c0 = v.cid_at[r];
+        uint32_t c = c0, last;
+        if (flat) {
+            last = v.clast0[c0];
+            if (r == s) v.clast[c0] = last;
+        } else {
+            c = gfind(v.cpar_d, c0);
+            last = *reinterpret_cast<volatile uint32_t *>(&v.clast[c]);
+        }
+        v.pstate[s] = make_uint4(s, c, last, skey[s]);
     }
 }
 
@@ -431,32 +553,29 @@ __global__ void __launch_bounds__(256) k_timeline_state(Work w, VarWork v) {
         T[j] = v.pstate[tl[j]];
 }
 
-__global__ void __launch_bounds__(256) k_group_last_reset(Work w, VarWork v) {
-    const Prob &P = *w.prob;
-    const uint32_t nt = P.ntiles;
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-        const Seg &g = w.seg[w.tile_seg[t]];
-        uint32_t begin, end;
-        tile_range(g, t, begin, end);
-        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x)
-            if (w.parent[s] == s) v.glast[s] = 0;
+// Exact last keys of the groups (when a round merged nothing): reset at
+// the roots, then each id's own last key raised into its root's.
+__global__ void __launch_bounds__(256) k_group_last_reset(VarWork v) {
+    const uint32_t n = *v.ncomp;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        if (v.cpar_d[c] == c) v.clast[c] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_group_last(VarWork v) {
+    const uint32_t n = *v.ncomp;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const uint32_t f = gfind(v.cpar_d, c), k = v.clast0[c];
+        if (*reinterpret_cast<volatile uint32_t *>(&v.clast[f]) < k) atomicMax(&v.clast[f], k);
     }
 }
 
-// A group's last key: only hits that could raise the stored maximum issue
-// the atomic (a large group would otherwise serialise on one address).
-__global__ void __launch_bounds__(256) k_group_last(Work w, VarWork v) {
-    const Prob &P = *w.prob;
-    const uint32_t nt = P.ntiles;
-    const uint32_t *skey = pick(w.keys, sorted_sel(P));
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-        const Seg &g = w.seg[w.tile_seg[t]];
-        uint32_t begin, end;
-        tile_range(g, t, begin, end);
-        for (uint32_t s = begin + threadIdx.x; s < end; s += blockDim.x) {
-            const uint32_t r = gfind(w.parent, s), k = skey[s];
-            if (*reinterpret_cast<volatile uint32_t *>(&v.glast[r]) < k) atomicMax(&v.glast[r], k);
-        }
+// The result on the hits' forest: each component's root hooked under its
+// group's root (an earlier position: ids follow the roots' order).
+__global__ void __launch_bounds__(256) k_comp_parents(Work w, VarWork v) {
+    const uint32_t n = *v.ncomp;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const uint32_t f = gfind(v.cpar_d, c);
+        if (f != c) w.parent[v.croot[c]] = v.croot[f];
     }
 }
 
@@ -479,29 +598,13 @@ __device__ __forceinline__ bool gunion_last(uint32_t *parent, uint32_t *glast, u
     }
 }
 
-// Apply the rule to one edge (hit s with key ks and current root rh, latest
-// earlier hit l on one of its 9 pixels); returns 1 if merged (rh then holds
-// s's new root), 0 if the groups already agree, 2 if the edge stays open
-// (its groups differ and the rule does not hold yet).
-__device__ __forceinline__ int global_edge(const Work &w, const VarWork &v, uint32_t ks, uint32_t dt, uint32_t s,
-                                           uint32_t &rh, uint32_t l) {
-    const uint32_t rl = gfind(w.parent, l);
-    if (rl == rh) return 0;
-    rh = gfind(w.parent, rh);   // a concurrent union may have moved s's root
-    if (rl == rh) return 0;
-    const uint32_t last = *reinterpret_cast<volatile uint32_t *>(&v.glast[rl]);
-    if ((uint64_t)ks <= (uint64_t)last + dt) {
-        gunion_last(w.parent, v.glast, s, l);
-        rh = gfind(w.parent, s);
-        return 1;
-    }
-    return 2;
-}
-
-// Append the warp's open edges to list `out` (one atomic per warp); on
+// Append the warp's open edges (a node of h's group, a node of its
+// neighbour's group, h's key) to list `out` (one atomic per warp); on
 // overflow the list is marked and the next round takes every hit again.
-__device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep, uint32_t s, uint32_t l) {
+__device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep, uint32_t a, uint32_t b,
+                                           uint32_t key) {
     uint2 *list = pick(v.edges, out);
+    uint32_t *keys = pick(v.ekey, out);
     const uint32_t m = __ballot_sync(0xffffffffu, keep);
     if (!m) return;
     const int lane = threadIdx.x & 31;
@@ -510,8 +613,12 @@ __device__ __forceinline__ void push_edges(const VarWork &v, int out, bool keep,
     base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
     const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
     if (keep) {
-        if (slot < v.edge_cap) list[slot] = make_uint2(s, l);
-        else v.changed[1] = 1u;
+        if (slot < v.edge_cap) {
+            list[slot] = make_uint2(a, b);
+            keys[slot] = key;
+        } else {
+            v.changed[1] = 1u;
+        }
     }
 }
 
@@ -586,12 +693,12 @@ __global__ void __launch_bounds__(256) k_global_first(Work w, VarWork v, int out
     for (uint32_t i0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32u; i0 < n; i0 += warps * 32u) {
         const uint32_t i = i0 + (uint32_t)lane;
         const bool valid = i < n;
-        const uint4 me = valid ? T[i] : make_uint4(0, 0, 0, 0);   // position, root, last, key
+        const uint4 me = valid ? T[i] : make_uint4(0, 0, 0, 0);   // position, group id, its last key, key
         const uint32_t p = valid ? tk[i] : 0xFFFFFFFFu;
         const uint32_t p0 = __shfl_sync(0xffffffffu, p, 0);
         const bool uniform = __all_sync(0xffffffffu, p == p0);
         const int px = (int)(p % W), py = (int)(p / W);
-        uint32_t rh = me.y;   // a node of h's group, moved towards its root as the round goes
+        uint32_t rh = me.y;   // an id of h's group, moved towards its root as the round goes
 #pragma unroll 1
         for (int d = 0; d < 9; ++d) {
             uint4 nb = make_uint4(0, 0, 0, 0);
@@ -619,13 +726,13 @@ __global__ void __launch_bounds__(256) k_global_first(Work w, VarWork v, int out
             int r = 0;
             uint32_t rl = nb.y;
             if (has && rl != rh) {
-                rl = gfind(w.parent, rl);
-                if (rl != rh) rh = gfind(w.parent, rh);   // h's group may have been hooked since
+                rl = gfind(v.cpar_d, rl);
+                if (rl != rh) rh = gfind(v.cpar_d, rh);   // h's group may have been joined since
                 if (rl != rh) {
                     bool ok = (uint64_t)me.w <= (uint64_t)nb.z + dt;
-                    if (!ok) ok = (uint64_t)me.w <= (uint64_t)*reinterpret_cast<volatile uint32_t *>(&v.glast[rl]) + dt;
+                    if (!ok) ok = (uint64_t)me.w <= (uint64_t)*reinterpret_cast<volatile uint32_t *>(&v.clast[rl]) + dt;
                     if (ok) {
-                        if (gunion_last(w.parent, v.glast, rh, rl)) r = 1;
+                        if (gunion_last(v.cpar_d, v.clast, rh, rl)) r = 1;
                         rh = min(rh, rl);
                     } else {
                         r = 2;
@@ -633,16 +740,17 @@ __global__ void __launch_bounds__(256) k_global_first(Work w, VarWork v, int out
                 }
             }
             changed |= r == 1;
-            push_edges(v, out, r == 2, me.x, rl);
+            push_edges(v, out, r == 2, rh, rl, me.w);
         }
     }
     if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&v.changed[0], 1u);
 }
 
-// A round over the open edges of list `in` only.
+// A round over the open edges of list `in` only: both ends' first steps
+// up the forest at once.
 __global__ void __launch_bounds__(256) k_global_list(Work w, VarWork v, int in) {
-    const uint32_t *skey = pick(w.keys, sorted_sel(*w.prob));
     const uint2 *list = pick(v.edges, in);
+    const uint32_t *keys = pick(v.ekey, in);
     const uint32_t dt = w.seg[0].dt;
     const unsigned long long n = v.ecount[in];
     const uint32_t cnt = n < v.edge_cap ? (uint32_t)n : v.edge_cap;
@@ -651,22 +759,48 @@ __global__ void __launch_bounds__(256) k_global_list(Work w, VarWork v, int in) 
     for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < cnt; e0 += stride) {
         const uint32_t e = e0 + threadIdx.x;
         const bool valid = e < cnt;
-        const uint2 ed = valid ? list[e] : make_uint2(0, 0);
-        int r = 0;
+        uint2 ed = make_uint2(0, 0);
+        uint32_t ks = 0, ux = 0, uy = 0;
         if (valid) {
-            uint32_t rh = gfind(w.parent, ed.x);
-            r = global_edge(w, v, skey[ed.x], dt, ed.x, rh, ed.y);
+            ed = list[e];
+            ks = keys[e];
+            ux = v.cpar_d[ed.x];
+            uy = v.cpar_d[ed.y];
+        }
+        int r = 0;
+        uint32_t rh = ed.x, rl = ed.y;
+        if (valid) {
+            rh = ux == ed.x ? ux : gfind(v.cpar_d, ux);
+            rl = uy == ed.y ? uy : gfind(v.cpar_d, uy);
+            if (rl != rh) {   // the rule on the group's last key as it stands (a lower bound)
+                const uint32_t last = *reinterpret_cast<volatile uint32_t *>(&v.clast[rl]);
+                if ((uint64_t)ks <= (uint64_t)last + dt) r = gunion_last(v.cpar_d, v.clast, rh, rl) ? 1 : 0;
+                else r = 2;
+            }
         }
         changed |= r == 1;
-        push_edges(v, 1 - in, r == 2, ed.x, ed.y);
+        push_edges(v, 1 - in, r == 2, rh, rl, ks);
     }
     if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&v.changed[0], 1u);
 }
 
-void launch_group_last(const Work &w, const VarWork &v, const Launch &L) {
-    k_group_last_reset<<<L.fit(k_group_last_reset, 256, 0), 256, 0, L.stream>>>(w, v);
-    k_group_last<<<L.fit(k_group_last, 256, 0), 256, 0, L.stream>>>(w, v);
+void launch_components(const Work &w, const VarWork &v, const Launch &L) {
+    k_comp_count<<<L.fit(k_comp_count, 256, 0), 256, 0, L.stream>>>(w, v);
+    k_comp_scan<<<1, 1024, 0, L.stream>>>(w, v);
+    k_comp_ids<<<L.fit(k_comp_ids, 256, 0), 256, 0, L.stream>>>(w, v);
+    k_comp_last<<<L.fit(k_comp_last, 256, 0), 256, 0, L.stream>>>(w, v);
+    L.mark("k_components");
+}
+
+void launch_group_last(const VarWork &v, const Launch &L) {
+    k_group_last_reset<<<L.fit(k_group_last_reset, 256, 0), 256, 0, L.stream>>>(v);
+    k_group_last<<<L.fit(k_group_last, 256, 0), 256, 0, L.stream>>>(v);
     L.mark("k_group_last");
+}
+
+void launch_comp_parents(const Work &w, const VarWork &v, const Launch &L) {
+    k_comp_parents<<<L.fit(k_comp_parents, 256, 0), 256, 0, L.stream>>>(w, v);
+    L.mark("k_comp_parents");
 }
 
 // One round: list `1 - in` (or, if full, every hit) into list `in`'s
