@@ -86,7 +86,7 @@ def path_bytes_per_hit(n_hits: int, n_clusters: int) -> float:
 # hashed on its own; the rest of that file (context bookkeeping, checkpoints)
 # and the host-side buffer filling are not part of any kernel.
 KERNEL_SOURCES = ("features.cu", "link.cu", "noalloc.cu", "prepare.cu", "radix.cu", "sortfast.cu",
-                  "tpc_internal.cuh", "variants.cu")
+                  "tpc_internal.cuh")   # variants.cu: (b)/(c) kernels, never launched by the step
 
 
 def kernel_source_sha() -> str:

@@ -54,6 +54,24 @@ def test_random_dense(variant, seed):
     check_against_oracle(hits, w, h, int(rng.integers(0, 40)), variant)
 
 
+@pytest.mark.parametrize("dt", [30, 400])
+def test_global_long_timelines_busy_neighbour(dt):
+    """(b) with pixel timelines of thousands of hits, so that warps take
+    whole 32-hit chunks of one pixel and carry their neighbour cursors from
+    chunk to chunk, next to a pixel firing 20 times as often: 32 hits of a
+    quiet pixel then span hundreds of the busy one's, past the 64-entry
+    window each lane searches first."""
+    rng = np.random.default_rng(77 + dt)
+    w = h = 6
+    n = 120_000
+    weights = np.ones(w * h)
+    weights[14] = 20.0
+    px = rng.choice(w * h, size=n, p=weights / weights.sum())
+    t = np.sort(rng.integers(0, n * 40, size=n))
+    hits = oracle.make_hits(px % w, px // w, t)
+    check_against_oracle(hits, w, h, dt, "global")
+
+
 @pytest.mark.parametrize("variant", ["global", "static"])
 def test_edge_cases(variant):
     one = oracle.make_hits([3], [2], [5])
@@ -98,7 +116,7 @@ def test_device_paths_are_reached():
     st = _gpu_stats(hits, 448, 512, 128, "static")
     assert st["windowed"] > 0 and st["window_fallbacks"] == 0, st
     st = _gpu_stats(hits, 448, 512, 128, "global")
-    assert st["rounds"] >= 3 and st["exact_checks"] >= 1, st
+    assert st["rounds"] >= 3 and st["exact_checks"] >= 1 and st["first_open_edges"] > 0, st
     rng = np.random.default_rng(31)
     same = random_hits(rng, 9000, 60, 40, 0)               # one ToA: every hit within dt of every other
     st = _gpu_stats(same, 60, 40, 0, "static")            # a 9000-hit component: the CTA sweep, global
