@@ -350,11 +350,13 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
 //
 // Components: each hit points to the smallest earlier neighbour it found (a
 // forest, since parents have smaller ranks, whose roots are the smallest
-// ranks of their trees); further neighbours go to an edge list.  After one
-// pointer-jumping pass over the forest, each listed edge is a lock-free union
-// that hooks the larger root under the smaller with compare-and-swap
-// (Jaiganesh & Burtscher's ECL-CC hooking), so the surviving root of a
-// component is its smallest rank, i.e. its earliest hit.  A list longer than
+// ranks of their trees); further neighbours go to an edge list.  Each listed
+// edge is then a lock-free union that hooks the larger root under the
+// smaller with compare-and-swap (Jaiganesh & Burtscher's ECL-CC hooking),
+// straight on that forest: the finds halve the paths they walk, which
+// shortens them for the finds after (a separate pointer-jumping pass over
+// every hit first measured slower), so the surviving root of a component is
+// its smallest rank, i.e. its earliest hit.  A list longer than
 // TAB_WALK (a pile on one pixel) or more edges than the list holds send the
 // tile to k_tile_link instead.  Only the table entries a tile touched are
 // reset afterwards (Algorithm 3 step 7).
@@ -362,7 +364,6 @@ constexpr int TAB_THREADS = 1024;
 constexpr uint16_t TAB_NONE = 0xFFFFu;
 constexpr int TAB_WALK = 64;
 constexpr int TAB_EDGES = 3 * TILE / 2;
-constexpr int CAND = 6;
 
 struct TabShared {
     uint16_t tab[TAB_CAP];           // head of each pixel's list (rank), or TAB_NONE
@@ -426,41 +427,36 @@ __device__ __forceinline__ bool tab_union(volatile uint32_t *par, uint32_t a, ui
     return false;
 }
 
+// List one extra edge (k, j) (rare: a second entry of a pixel's list).
+__device__ __forceinline__ void tab_edge(TabShared &S, uint32_t k, uint32_t j) {
+    const uint32_t slot = atomicAdd(&S.nedges, 1u);
+    if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | j;
+}
+
 // The walk of hit k (key `key`; `centre` = its pixel's table entry, rows W2
-// entries apart): its smallest earlier neighbour within dt becomes `parent`,
-// further ones go to cand[] (more than CAND straight to the edge list).  The
-// heads of the 9 lists are read first (independent loads), then the head
-// entries without loops or branches around the loads; lists with a second
-// entry (a pixel hit more than once in the tile: rare) are walked afterwards.
-__device__ __forceinline__ void tab_walk(TabShared &S, uint32_t k, uint32_t key, uint32_t centre,
-                                         uint32_t W2, uint32_t dt, uint32_t &parent,
-                                         uint32_t (&cand)[CAND], int &nc) {
-    auto consider = [&](uint32_t j) {   // j: an earlier neighbour within dt
-        uint32_t other = j;
-        if (parent == k) { parent = j; return; }
-        if (j < parent) { other = parent; parent = j; }
-        if (nc < CAND) {   // constant indices keep cand in registers
-#pragma unroll
-            for (int i = 0; i < CAND; ++i)
-                if (i == nc) cand[i] = other;
-            ++nc;
-        } else {   // rare: straight to the edge list
-            const uint32_t slot = atomicAdd(&S.nedges, 1u);
-            if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | other;
-        }
-    };
-    uint32_t hd[9];
+// entries apart).  Returns its parent: the smallest earlier neighbour within
+// dt, or k if it has none.  Every other earlier neighbour within dt is an
+// extra edge (k, j).  The heads of the 9 lists are read first (independent
+// loads), then tested without branches: bit n of `em` marks head n as an
+// extra edge, for tab_emit to list.  Lists with a second entry (a pixel hit
+// more than once in the tile: rare) are walked afterwards, their extra edges
+// listed at once.
+__device__ __forceinline__ uint32_t tab_walk(TabShared &S, uint32_t k, uint32_t key, uint32_t centre,
+                                             uint32_t W2, uint32_t dt, uint32_t (&hd)[9], uint32_t &em) {
 #pragma unroll
     for (int n = 0; n < 9; ++n) hd[n] = S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)];
-    uint32_t more = 0;
+    uint32_t more = 0, okm = 0, mn = TAB_NONE, pn = 9;   // pn: the head holding mn (9: none)
 #pragma unroll
     for (int n = 0; n < 9; ++n) {
         const uint32_t j = hd[n];
         const uint32_t jm = j & (TILE - 1);   // an empty head reads a harmless entry
         const uint32_t kj = S.key[jm], nx = S.next[jm];
-        const bool has = j != TAB_NONE;
-        more |= (has && nx != TAB_NONE ? 1u : 0u) << n;
-        if (has && j < k && key - kj <= dt) consider(j);
+        more |= (j != TAB_NONE && nx != TAB_NONE ? 1u : 0u) << n;
+        const bool ok = j < k && key - kj <= dt;   // an empty head (TAB_NONE) is never below k
+        okm |= (ok ? 1u : 0u) << n;
+        const bool lower = ok && j < mn;
+        mn = lower ? j : mn;
+        pn = lower ? (uint32_t)n : pn;
     }
     while (more) {   // lists holding more than one hit
         const int n = __ffs(more) - 1;
@@ -471,30 +467,44 @@ __device__ __forceinline__ void tab_walk(TabShared &S, uint32_t k, uint32_t key,
             if (m == n) h = hd[m];
         uint32_t j = S.next[h];
         int steps = 1;
-        for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps)
-            if (j < k && key - S.key[j] <= dt) consider(j);
+        for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps) {
+            if (j < k && key - S.key[j] <= dt) {
+                uint32_t e = j;
+                if (j < mn) {   // a new parent: the one it replaces becomes an edge
+                    e = pn < 9 ? TAB_NONE : mn;   // (a head's edge is listed by tab_emit)
+                    mn = j;
+                    pn = 9;
+                }
+                if (e != TAB_NONE) tab_edge(S, k, e);
+            }
+        }
         if (j != TAB_NONE) S.overflow = 1;
     }
+    em = okm & ~(1u << pn);
+    return mn == TAB_NONE ? k : mn;
 }
 
-// Append the warp's candidate edges to the shared list; every lane calls
-// this (a ballot per candidate slot).  Candidate c of a lane is listed if
-// bit c of its mask is set.
-__device__ __forceinline__ void tab_append(TabShared &S, uint32_t k, const uint32_t (&cand)[CAND], uint32_t keep,
-                                           int lane) {
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    const uint32_t most = __reduce_or_sync(0xffffffffu, keep);
+// List the extra edges (k, head n) for the bits n of `em`; every lane calls
+// this.  A lane's first edge takes a slot from one ballot of the warp,
+// further ones (a hit with three or more earlier neighbours: rare) an atomic
+// each.
+__device__ __forceinline__ void tab_emit(TabShared &S, uint32_t k, const uint32_t (&hd)[9], uint32_t em,
+                                         int lane) {
+    const uint32_t m = __ballot_sync(0xffffffffu, em != 0);
+    if (!m) return;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&S.nedges, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    uint32_t slot = base + __popc(m & ((1u << lane) - 1u));
+    while (em) {
+        const int n = __ffs(em) - 1;
+        em &= em - 1;
+        uint32_t j = hd[0];
 #pragma unroll
-    for (int c = 0; c < CAND; ++c) {
-        if (!(most >> c)) break;
-        const bool has = (keep >> c) & 1u;
-        const uint32_t m = __ballot_sync(0xffffffffu, has);
-        if (!m) continue;
-        uint32_t slot0 = 0;
-        if (lane == 0) slot0 = atomicAdd(&S.nedges, (uint32_t)__popc(m));
-        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-        const uint32_t slot = slot0 + __popc(m & lt_mask);
-        if (has && slot < TAB_EDGES) S.edges[slot] = (k << 16) | cand[c];
+        for (int q = 1; q < 9; ++q)
+            if (q == n) j = hd[q];
+        if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | j;
+        if (em) slot = atomicAdd(&S.nedges, 1u);
     }
 }
 
@@ -541,14 +551,9 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                uint32_t parent = k, cand[CAND], keep = 0;
-                int nc = 0;
-                if (k < n_t) {
-                    tab_walk(S, k, kv[q], tab_pid(pv[q], W), W2, dt, parent, cand, nc);
-                    keep = (1u << nc) - 1u;
-                    S.par[k] = parent;
-                }
-                tab_append(S, k, cand, keep, lane);
+                uint32_t hd[9], em = 0;
+                if (k < n_t) S.par[k] = tab_walk(S, k, kv[q], tab_pid(pv[q], W), W2, dt, hd, em);
+                tab_emit(S, k, hd, em, lane);
             }
         } else {
             // band by band: a band's table holds its rows and the rows just
@@ -581,18 +586,14 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 const uint32_t cnt = S.wl_count[b];
                 for (uint32_t base = 0; base < cnt; base += TAB_THREADS) {
                     const uint32_t idx = base + threadIdx.x;
-                    uint32_t k = 0, parent = 0, cand[CAND], keep = 0;
-                    int nc = 0;
+                    uint32_t k = 0, hd[9], em = 0;
                     if (idx < cnt) {
                         k = S.wl[idx];
-                        parent = k;
                         const uint32_t pix = S.pix[k];
-                        tab_walk(S, k, S.key[k], ((pix >> 16) + 1 - y0) * W2 + (pix & 0xFFFFu) + 1, W2, dt,
-                                 parent, cand, nc);
-                        keep = (1u << nc) - 1u;
-                        S.par[k] = parent;
+                        S.par[k] = tab_walk(S, k, S.key[k], ((pix >> 16) + 1 - y0) * W2 + (pix & 0xFFFFu) + 1,
+                                            W2, dt, hd, em);
                     }
-                    tab_append(S, k, cand, keep, lane);
+                    tab_emit(S, k, hd, em, lane);
                 }
                 __syncthreads();
 #pragma unroll
@@ -608,13 +609,6 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
         bool redo = S.overflow || S.nedges > TAB_EDGES;
         if (!redo) {
             const uint32_t ne = S.nedges;
-            // flatten the forest, then one union per extra edge
-#pragma unroll
-            for (int q = 0; q < ITEMS; ++q) {
-                const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                if (k < n_t) vpar[k] = tab_root(vpar, k);
-            }
-            __syncthreads();
             bool ok = true;
             // edges are listed warp by warp, so neighbouring entries tend to
             // share roots: lanes take entries ne / 32 apart (fewer colliding

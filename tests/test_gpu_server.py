@@ -47,16 +47,31 @@ def _run_server(server, streams, ids):
 
 
 def test_server_tight_budget_queues_and_matches_alone_and_oracle():
-    streams = synth.cfg3(hits_per_stream=400_000, n_streams=4, seed=77, chunk_lo=65536,
-                         chunk_hi=262144)
-    budget = 200 << 20   # room for about two 256k-hit chunks in flight next to the carries
+    """Two streams whose first chunks (1 Mi hits each) cannot run together
+    under the budget: a 1 Mi-hit first chunk holds about 280 B per hit while
+    it runs (work arrays, outputs, the stream's carry and chunk buffers), and
+    about half of that stays held by the idle stream (its carry and chunk
+    buffers).  The second stream's first chunk is submitted microseconds
+    after the first one, which takes milliseconds, so it must wait at the
+    head of the queue; once the first finishes, the idle stream's work
+    arrays are released and it fits.  The later chunks (64k-128k hits) run
+    side by side."""
+    rng = np.random.default_rng(77)
+    streams = []
+    for hits, _, t in synth.cfg3(hits_per_stream=3_000_000, n_streams=2, seed=77):
+        sizes = [2**20]
+        while sum(sizes) < len(hits):
+            sizes.append(min(int(rng.integers(65536, 131073)), len(hits) - sum(sizes)))
+        streams.append((hits, np.array(sizes), t))
+    budget = 512 << 20
     with Server(budget) as srv:
         ids = [srv.add_stream(256, 256, 128, t) for _, _, t in streams]
         got = _run_server(srv, streams, ids)
         st = srv.stats()
-    assert st["waits"] > 0, "the budget should have made chunks wait"
+    assert st["waits"] > 0, f"the budget should have made chunks wait: {st}"
+    assert st["releases"] > 0, st
     assert st["peak"] <= budget
-    assert st["completed"] == st["submitted"] and st["failed"] == 0 and st["rejected"] == 0
+    assert st["completed"] == st["submitted"] and st["failed"] == 0 and st["rejected"] == 0, st
     for k, (hits, sizes, t) in zip(ids, streams):
         idx, lab, rec = got[k]
         check_stream_result(hits, idx, lab, rec)   # against the oracle on the whole stream
