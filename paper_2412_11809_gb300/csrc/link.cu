@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(LINK_THREADS) k_tile_link(Work w) {
 // tile to k_tile_link instead.  Only the table entries a tile touched are
 // reset afterwards (Algorithm 3 step 7).
 constexpr int TAB_THREADS = 1024;
-constexpr uint16_t TAB_NONE = 0xFFFFu;
+constexpr uint16_t TAB_NONE = 0x7FFFu;   // empty list / end of list
+constexpr uint32_t TAB_MORE = 0x8000u;   // table entry flag: the list holds a second hit
 constexpr int TAB_WALK = 64;
 constexpr int TAB_EDGES = 3 * TILE / 2;
 
@@ -384,15 +385,19 @@ __device__ __forceinline__ uint32_t tab_pid(uint32_t pix, uint32_t W) {
     return ((pix >> 16) + 1) * (W + 2) + (pix & 0xFFFFu) + 1;
 }
 
-// push rank k on pixel pid's list; returns the previous head
+// push rank k on pixel pid's list; returns the previous head (a rank, or
+// TAB_NONE).  The new head entry carries TAB_MORE when the list already held
+// a hit, so walks see multi-hit lists without reading the link array.
 __device__ __forceinline__ uint16_t tab_push(uint16_t *tab, uint32_t pid, uint16_t k) {
     uint32_t *word = reinterpret_cast<uint32_t *>(tab) + (pid >> 1);
     const uint32_t shift = (pid & 1u) * 16u;
     uint32_t old = *reinterpret_cast<volatile uint32_t *>(word);
     while (true) {
-        const uint32_t nv = (old & ~(0xFFFFu << shift)) | ((uint32_t)k << shift);
+        const uint32_t prev = (old >> shift) & 0x7FFFu;
+        const uint32_t ent = (uint32_t)k | (prev != TAB_NONE ? TAB_MORE : 0u);
+        const uint32_t nv = (old & ~(0xFFFFu << shift)) | (ent << shift);
         const uint32_t seen = atomicCAS(word, old, nv);
-        if (seen == old) return (uint16_t)(old >> shift);
+        if (seen == old) return (uint16_t)prev;
         old = seen;
     }
 }
@@ -448,10 +453,10 @@ __device__ __forceinline__ uint32_t tab_walk(TabShared &S, uint32_t k, uint32_t 
     uint32_t more = 0, okm = 0, mn = TAB_NONE, pn = 9;   // pn: the head holding mn (9: none)
 #pragma unroll
     for (int n = 0; n < 9; ++n) {
+        more |= (hd[n] >> 15) << n;           // TAB_MORE
+        hd[n] &= 0x7FFFu;
         const uint32_t j = hd[n];
-        const uint32_t jm = j & (TILE - 1);   // an empty head reads a harmless entry
-        const uint32_t kj = S.key[jm], nx = S.next[jm];
-        more |= (j != TAB_NONE && nx != TAB_NONE ? 1u : 0u) << n;
+        const uint32_t kj = S.key[j & (TILE - 1)];   // an empty head reads a harmless entry
         const bool ok = j < k && key - kj <= dt;   // an empty head (TAB_NONE) is never below k
         okm |= (ok ? 1u : 0u) << n;
         const bool lower = ok && j < mn;
@@ -481,6 +486,60 @@ __device__ __forceinline__ uint32_t tab_walk(TabShared &S, uint32_t k, uint32_t 
         if (j != TAB_NONE) S.overflow = 1;
     }
     em = okm & ~(1u << pn);
+    return mn == TAB_NONE ? k : mn;
+}
+
+// Extra edges of one-band sensors go to per-thread buffers of TAB_EB
+// entries in the pixel array (which only banded sensors use), slot-major:
+// entry s of thread t at [s * TAB_THREADS + t], holding q << 12 | j for the
+// edge (q * TAB_THREADS + t, j); a thread with more goes to the shared list.
+constexpr int TAB_EB = 8;
+
+// The walk of hit k = q * TAB_THREADS + threadIdx.x on a one-band sensor:
+// as tab_walk, but every extra edge is listed as soon as it is known (at
+// each earlier neighbour within dt: the neighbour, or the parent it
+// replaces), into the thread's buffer (count ecnt).
+__device__ __forceinline__ uint32_t tab_walk_buf(TabShared &S, uint32_t q, uint32_t k, uint32_t key,
+                                                 uint32_t centre, uint32_t W2, uint32_t dt, uint32_t &ecnt) {
+    uint16_t *eb = reinterpret_cast<uint16_t *>(S.pix);
+    auto edge = [&](uint32_t e) {
+        if (ecnt < TAB_EB) eb[ecnt * TAB_THREADS + threadIdx.x] = (uint16_t)(q << 12 | e);
+        else tab_edge(S, k, e);
+        ++ecnt;
+    };
+    uint32_t hd[9];
+#pragma unroll
+    for (int n = 0; n < 9; ++n) hd[n] = S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)];
+    uint32_t more = 0, mn = TAB_NONE;
+#pragma unroll
+    for (int n = 0; n < 9; ++n) {
+        more |= (hd[n] >> 15) << n;           // TAB_MORE
+        hd[n] &= 0x7FFFu;
+        const uint32_t j = hd[n];
+        const uint32_t kj = S.key[j & (TILE - 1)];   // an empty head reads a harmless entry
+        const bool ok = j < k && key - kj <= dt;   // an empty head (TAB_NONE) is never below k
+        const uint32_t e = j < mn ? mn : j;        // the new edge: the old parent, or j
+        if (ok && e != TAB_NONE) edge(e);
+        mn = ok && j < mn ? j : mn;
+    }
+    while (more) {   // lists holding more than one hit
+        const int n = __ffs(more) - 1;
+        more &= more - 1;
+        uint32_t h = hd[0];
+#pragma unroll
+        for (int m = 1; m < 9; ++m)   // a select, not an indexed load: hd stays in registers
+            if (m == n) h = hd[m];
+        uint32_t j = S.next[h];
+        int steps = 1;
+        for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps) {
+            if (j < k && key - S.key[j] <= dt) {
+                const uint32_t e = j < mn ? mn : j;
+                if (e != TAB_NONE) edge(e);
+                mn = j < mn ? j : mn;
+            }
+        }
+        if (j != TAB_NONE) S.overflow = 1;
+    }
     return mn == TAB_NONE ? k : mn;
 }
 
@@ -517,7 +576,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
     const uint32_t *skey = pick(w.keys, sorted_sel(P));
     const int lane = threadIdx.x & 31;
     for (uint32_t i = threadIdx.x; i < TAB_CAP / 2; i += TAB_THREADS)
-        reinterpret_cast<uint32_t *>(S.tab)[i] = 0xFFFFFFFFu;
+        reinterpret_cast<uint32_t *>(S.tab)[i] = 0x7FFF7FFFu;
     __syncthreads();
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const Seg &g = w.seg[w.tile_seg[t]];
@@ -536,6 +595,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             if (k < n_t) { kv[q] = skey[begin + k]; pv[q] = w.spix[begin + k]; }
         }
         if (threadIdx.x == 0) { S.overflow = 0; S.nedges = 0; }
+        uint32_t ecnt = 0;   // one band: this thread's buffered extra edges
         if (nb == 1) {
             // the whole sensor in one table: push every hit, then walk each
             // from registers
@@ -551,9 +611,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                uint32_t hd[9], em = 0;
-                if (k < n_t) S.par[k] = tab_walk(S, k, kv[q], tab_pid(pv[q], W), W2, dt, hd, em);
-                tab_emit(S, k, hd, em, lane);
+                if (k < n_t) S.par[k] = tab_walk_buf(S, q, k, kv[q], tab_pid(pv[q], W), W2, dt, ecnt);
             }
         } else {
             // band by band: a band's table holds its rows and the rows just
@@ -619,6 +677,11 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 if (idx >= ne) continue;
                 const uint32_t ed = S.edges[idx];
                 ok &= tab_union(vpar, ed >> 16, ed & 0xFFFFu);
+            }
+            const uint16_t *eb = reinterpret_cast<const uint16_t *>(S.pix);
+            for (uint32_t i = 0; i < ecnt && i < TAB_EB; ++i) {   // this thread's buffered edges
+                const uint32_t e = eb[i * TAB_THREADS + threadIdx.x];
+                ok &= tab_union(vpar, (e >> 12) * TAB_THREADS + threadIdx.x, e & (TILE - 1));
             }
             redo = !__syncthreads_and(ok);
         }
