@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(ACC_THREADS, ACC_SPAN >= 2048 ? 2 : 4) k_accum
                     rr[q] = w.parent[s];
                     px[q] = w.spix[s];
                     tt[q] = w.stot[s];
-                    kk[q] = skey[s];
+                    kk[q] = want_max ? skey[s] : 0u;   // the last key only matters when streaming
                     ps[q] = sidx[s];
                 }
             }

@@ -371,7 +371,7 @@ struct TabShared {
     uint32_t key[TILE];              // per rank: key
     uint16_t next[TILE];             // per rank: next rank on the same pixel
     uint32_t par[TILE];              // forest over ranks
-    uint32_t edges[TAB_EDGES];       // extra edges, k << 16 | j
+    uint32_t edges[TAB_EDGES];       // banded: extra-edge buffers, then the shared list (k << 16 | j)
     uint32_t pix[TILE];              // per rank: pixel (banded sensors)
     uint16_t wl[TILE];               // ranks walked in the current band
     uint32_t wl_count[TAB_MAX_BANDS];
@@ -432,79 +432,48 @@ __device__ __forceinline__ bool tab_union(volatile uint32_t *par, uint32_t a, ui
     return false;
 }
 
-// List one extra edge (k, j) (rare: a second entry of a pixel's list).
-__device__ __forceinline__ void tab_edge(TabShared &S, uint32_t k, uint32_t j) {
-    const uint32_t slot = atomicAdd(&S.nedges, 1u);
-    if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | j;
-}
+// Extra edges.  Each thread lists the extra edges of the hits it walks into
+// a buffer of its own as soon as they are known, so no warp-wide pass lists
+// them; the union phase then takes each thread's buffer.  One-band sensors:
+// a thread walks its own hits q * TAB_THREADS + t, so an entry is
+// q << 12 | j (16 bits, TAB_EB per thread in the pixel array, which only
+// banded sensors use).  Banded sensors: a thread walks listed hits, so an
+// entry is k << 12 | j (32 bits, TAB_EBB per thread in the first part of the
+// edge array).  Entry s of thread t sits at [s * TAB_THREADS + t].  Edges
+// beyond a buffer go to the shared list (the rest of the edge array).
+constexpr int TAB_EB = 8;
+constexpr int TAB_EBB = 3;
+constexpr uint32_t TAB_LIST_BAND = TAB_EDGES - TAB_EBB * TAB_THREADS;   // shared-list entries, banded
+static_assert(TAB_EB * TAB_THREADS * 2 <= TILE * 4, "one-band buffers fit the pixel array");
+static_assert(TAB_LIST_BAND > 0, "banded buffers leave a shared list");
+
+template <bool BAND>
+__device__ __forceinline__ uint32_t *tab_list(TabShared &S) { return BAND ? S.edges + TAB_EBB * TAB_THREADS : S.edges; }
+template <bool BAND>
+__device__ __forceinline__ uint32_t tab_list_cap() { return BAND ? TAB_LIST_BAND : (uint32_t)TAB_EDGES; }
 
 // The walk of hit k (key `key`; `centre` = its pixel's table entry, rows W2
-// entries apart).  Returns its parent: the smallest earlier neighbour within
-// dt, or k if it has none.  Every other earlier neighbour within dt is an
-// extra edge (k, j).  The heads of the 9 lists are read first (independent
-// loads), then tested without branches: bit n of `em` marks head n as an
-// extra edge, for tab_emit to list.  Lists with a second entry (a pixel hit
-// more than once in the tile: rare) are walked afterwards, their extra edges
-// listed at once.
-__device__ __forceinline__ uint32_t tab_walk(TabShared &S, uint32_t k, uint32_t key, uint32_t centre,
-                                             uint32_t W2, uint32_t dt, uint32_t (&hd)[9], uint32_t &em) {
-#pragma unroll
-    for (int n = 0; n < 9; ++n) hd[n] = S.tab[centre + (n / 3 - 1) * (int)W2 + (n % 3 - 1)];
-    uint32_t more = 0, okm = 0, mn = TAB_NONE, pn = 9;   // pn: the head holding mn (9: none)
-#pragma unroll
-    for (int n = 0; n < 9; ++n) {
-        more |= (hd[n] >> 15) << n;           // TAB_MORE
-        hd[n] &= 0x7FFFu;
-        const uint32_t j = hd[n];
-        const uint32_t kj = S.key[j & (TILE - 1)];   // an empty head reads a harmless entry
-        const bool ok = j < k && key - kj <= dt;   // an empty head (TAB_NONE) is never below k
-        okm |= (ok ? 1u : 0u) << n;
-        const bool lower = ok && j < mn;
-        mn = lower ? j : mn;
-        pn = lower ? (uint32_t)n : pn;
-    }
-    while (more) {   // lists holding more than one hit
-        const int n = __ffs(more) - 1;
-        more &= more - 1;
-        uint32_t h = hd[0];
-#pragma unroll
-        for (int m = 1; m < 9; ++m)   // a select, not an indexed load: hd stays in registers
-            if (m == n) h = hd[m];
-        uint32_t j = S.next[h];
-        int steps = 1;
-        for (; j != TAB_NONE && steps < TAB_WALK; j = S.next[j], ++steps) {
-            if (j < k && key - S.key[j] <= dt) {
-                uint32_t e = j;
-                if (j < mn) {   // a new parent: the one it replaces becomes an edge
-                    e = pn < 9 ? TAB_NONE : mn;   // (a head's edge is listed by tab_emit)
-                    mn = j;
-                    pn = 9;
-                }
-                if (e != TAB_NONE) tab_edge(S, k, e);
-            }
-        }
-        if (j != TAB_NONE) S.overflow = 1;
-    }
-    em = okm & ~(1u << pn);
-    return mn == TAB_NONE ? k : mn;
-}
-
-// Extra edges of one-band sensors go to per-thread buffers of TAB_EB
-// entries in the pixel array (which only banded sensors use), slot-major:
-// entry s of thread t at [s * TAB_THREADS + t], holding q << 12 | j for the
-// edge (q * TAB_THREADS + t, j); a thread with more goes to the shared list.
-constexpr int TAB_EB = 8;
-
-// The walk of hit k = q * TAB_THREADS + threadIdx.x on a one-band sensor:
-// as tab_walk, but every extra edge is listed as soon as it is known (at
-// each earlier neighbour within dt: the neighbour, or the parent it
-// replaces), into the thread's buffer (count ecnt).
-__device__ __forceinline__ uint32_t tab_walk_buf(TabShared &S, uint32_t q, uint32_t k, uint32_t key,
-                                                 uint32_t centre, uint32_t W2, uint32_t dt, uint32_t &ecnt) {
-    uint16_t *eb = reinterpret_cast<uint16_t *>(S.pix);
+// entries apart; q: its item when the thread walks its own hits).  Returns
+// its parent: the smallest earlier neighbour within dt, or k if it has none.
+// Every other earlier neighbour within dt is an extra edge (k, j), listed
+// at the neighbour that reveals it (the neighbour itself, or the parent it
+// displaces).  The heads of the 9 lists are read first (independent loads),
+// then tested without branches: an empty head (TAB_NONE) is a rank above
+// every hit.  Lists whose head entry carries TAB_MORE hold further hits (a
+// pixel hit more than once in the tile: rare) and are walked afterwards.
+template <bool BAND>
+__device__ __forceinline__ uint32_t tab_walk(TabShared &S, uint32_t q, uint32_t k, uint32_t key, uint32_t centre,
+                                             uint32_t W2, uint32_t dt, uint32_t &ecnt) {
     auto edge = [&](uint32_t e) {
-        if (ecnt < TAB_EB) eb[ecnt * TAB_THREADS + threadIdx.x] = (uint16_t)(q << 12 | e);
-        else tab_edge(S, k, e);
+        if (BAND) {
+            if (ecnt < TAB_EBB) S.edges[ecnt * TAB_THREADS + threadIdx.x] = k << 12 | e;
+        } else {
+            if (ecnt < TAB_EB) reinterpret_cast<uint16_t *>(S.pix)[ecnt * TAB_THREADS + threadIdx.x] = (uint16_t)(q << 12 | e);
+        }
+        if (ecnt >= (BAND ? TAB_EBB : TAB_EB)) {   // the shared list
+            const uint32_t slot = atomicAdd(&S.nedges, 1u);
+            if (slot < tab_list_cap<BAND>()) tab_list<BAND>(S)[slot] = (k << 16) | e;
+        }
         ++ecnt;
     };
     uint32_t hd[9];
@@ -516,8 +485,8 @@ __device__ __forceinline__ uint32_t tab_walk_buf(TabShared &S, uint32_t q, uint3
         more |= (hd[n] >> 15) << n;           // TAB_MORE
         hd[n] &= 0x7FFFu;
         const uint32_t j = hd[n];
-        const uint32_t kj = S.key[j & (TILE - 1)];   // an empty head reads a harmless entry
-        const bool ok = j < k && key - kj <= dt;   // an empty head (TAB_NONE) is never below k
+        bool ok = false;                           // an empty head (TAB_NONE) is never below k
+        if (j < k) ok = key - S.key[j] <= dt;
         const uint32_t e = j < mn ? mn : j;        // the new edge: the old parent, or j
         if (ok && e != TAB_NONE) edge(e);
         mn = ok && j < mn ? j : mn;
@@ -541,30 +510,6 @@ __device__ __forceinline__ uint32_t tab_walk_buf(TabShared &S, uint32_t q, uint3
         if (j != TAB_NONE) S.overflow = 1;
     }
     return mn == TAB_NONE ? k : mn;
-}
-
-// List the extra edges (k, head n) for the bits n of `em`; every lane calls
-// this.  A lane's first edge takes a slot from one ballot of the warp,
-// further ones (a hit with three or more earlier neighbours: rare) an atomic
-// each.
-__device__ __forceinline__ void tab_emit(TabShared &S, uint32_t k, const uint32_t (&hd)[9], uint32_t em,
-                                         int lane) {
-    const uint32_t m = __ballot_sync(0xffffffffu, em != 0);
-    if (!m) return;
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&S.nedges, (uint32_t)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    uint32_t slot = base + __popc(m & ((1u << lane) - 1u));
-    while (em) {
-        const int n = __ffs(em) - 1;
-        em &= em - 1;
-        uint32_t j = hd[0];
-#pragma unroll
-        for (int q = 1; q < 9; ++q)
-            if (q == n) j = hd[q];
-        if (slot < TAB_EDGES) S.edges[slot] = (k << 16) | j;
-        if (em) slot = atomicAdd(&S.nedges, 1u);
-    }
 }
 
 __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
@@ -611,7 +556,7 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const uint32_t k = q * TAB_THREADS + threadIdx.x;
-                if (k < n_t) S.par[k] = tab_walk_buf(S, q, k, kv[q], tab_pid(pv[q], W), W2, dt, ecnt);
+                if (k < n_t) S.par[k] = tab_walk<false>(S, q, k, kv[q], tab_pid(pv[q], W), W2, dt, ecnt);
             }
         } else {
             // band by band: a band's table holds its rows and the rows just
@@ -644,14 +589,12 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
                 const uint32_t cnt = S.wl_count[b];
                 for (uint32_t base = 0; base < cnt; base += TAB_THREADS) {
                     const uint32_t idx = base + threadIdx.x;
-                    uint32_t k = 0, hd[9], em = 0;
                     if (idx < cnt) {
-                        k = S.wl[idx];
+                        const uint32_t k = S.wl[idx];
                         const uint32_t pix = S.pix[k];
-                        S.par[k] = tab_walk(S, k, S.key[k], ((pix >> 16) + 1 - y0) * W2 + (pix & 0xFFFFu) + 1,
-                                            W2, dt, hd, em);
+                        S.par[k] = tab_walk<true>(S, 0, k, S.key[k],
+                                                  ((pix >> 16) + 1 - y0) * W2 + (pix & 0xFFFFu) + 1, W2, dt, ecnt);
                     }
-                    tab_emit(S, k, hd, em, lane);
                 }
                 __syncthreads();
 #pragma unroll
@@ -664,24 +607,33 @@ __global__ void __launch_bounds__(TAB_THREADS, 1) k_tile_link_table(Work w) {
             }
         }
         __syncthreads();
-        bool redo = S.overflow || S.nedges > TAB_EDGES;
+        const uint32_t *list = nb == 1 ? tab_list<false>(S) : tab_list<true>(S);
+        bool redo = S.overflow || S.nedges > (nb == 1 ? tab_list_cap<false>() : tab_list_cap<true>());
         if (!redo) {
             const uint32_t ne = S.nedges;
             bool ok = true;
-            // edges are listed warp by warp, so neighbouring entries tend to
-            // share roots: lanes take entries ne / 32 apart (fewer colliding
+            // the shared list (edges beyond the threads' buffers) is filled
+            // warp by warp, so neighbouring entries tend to share roots:
+            // lanes take entries ne / 32 apart (fewer colliding
             // compare-and-swaps within a warp)
             const uint32_t ccol = (ne + 31) >> 5;
             for (uint32_t e = threadIdx.x; e < 32 * ccol; e += TAB_THREADS) {
                 const uint32_t idx = (e & 31) * ccol + (e >> 5);
                 if (idx >= ne) continue;
-                const uint32_t ed = S.edges[idx];
+                const uint32_t ed = list[idx];
                 ok &= tab_union(vpar, ed >> 16, ed & 0xFFFFu);
             }
-            const uint16_t *eb = reinterpret_cast<const uint16_t *>(S.pix);
-            for (uint32_t i = 0; i < ecnt && i < TAB_EB; ++i) {   // this thread's buffered edges
-                const uint32_t e = eb[i * TAB_THREADS + threadIdx.x];
-                ok &= tab_union(vpar, (e >> 12) * TAB_THREADS + threadIdx.x, e & (TILE - 1));
+            if (nb == 1) {   // this thread's buffered edges
+                const uint16_t *eb = reinterpret_cast<const uint16_t *>(S.pix);
+                for (uint32_t i = 0; i < ecnt && i < TAB_EB; ++i) {
+                    const uint32_t e = eb[i * TAB_THREADS + threadIdx.x];
+                    ok &= tab_union(vpar, (e >> 12) * TAB_THREADS + threadIdx.x, e & (TILE - 1));
+                }
+            } else {
+                for (uint32_t i = 0; i < ecnt && i < TAB_EBB; ++i) {
+                    const uint32_t e = S.edges[i * TAB_THREADS + threadIdx.x];
+                    ok &= tab_union(vpar, e >> 12, e & (TILE - 1));
+                }
             }
             redo = !__syncthreads_and(ok);
         }
