@@ -32,7 +32,10 @@ constexpr int acc_smem() {
 // records it by input position for the label pass, and sums into shared-
 // memory slots of the roots inside the span (a root precedes its cluster's
 // hits); hits of one cluster within a warp are combined first (match.any +
-// redux), so a burst of one track does not serialise on one slot.  One
+// redux) when there are three or more of them, so a burst of one track does
+// not serialise on one slot, while the small groups of a dense stream (where
+// each group's reductions would run one group after another) add their hits
+// one by one.  One
 // partial per root then goes to the global slots; hits whose root lies
 // before the span go there directly.  The global slots of tile roots were
 // zeroed by the tile-link kernels.  Size and sum ToT share one 64-bit
@@ -106,7 +109,12 @@ __global__ void __launch_bounds__(ACC_THREADS, ACC_SPAN >= 2048 ? 2 : 4) k_accum
                 uint32_t sum_tot = tot, mn = ps[q], mx = kk[q];
                 unsigned long long wx = (unsigned long long)tot * (pix & 0xFFFFu);
                 unsigned long long wy = (unsigned long long)tot * (pix >> 16);
-                if (cnt > 1) {   // combine this cluster's hits of the warp
+                // combine this cluster's hits of the warp when there are
+                // enough of them to contend; smaller groups add their hits
+                // one by one (a group reduction runs once per distinct group)
+                const bool agg = cnt >= 3u;
+                uint32_t c = 1;
+                if (agg) {
                     const uint32_t wx32 = tot * (pix & 0xFFFFu), wy32 = tot * (pix >> 16);
                     sum_tot = __reduce_add_sync(peers, tot);
                     wx = ((unsigned long long)__reduce_add_sync(peers, wx32 >> 16) << 16) +
@@ -115,18 +123,19 @@ __global__ void __launch_bounds__(ACC_THREADS, ACC_SPAN >= 2048 ? 2 : 4) k_accum
                          __reduce_add_sync(peers, wy32 & 0xFFFFu);
                     mn = __reduce_min_sync(peers, mn);
                     if (want_max) mx = __reduce_max_sync(peers, mx);
+                    c = cnt;
+                    if (lane != __ffs(peers) - 1) continue;
                 }
-                if (lane != __ffs(peers) - 1) continue;
                 if (r >= b) {
                     const uint32_t k = r - b;
-                    atomicAdd(&a_st[k], (unsigned long long)cnt << 32 | sum_tot);
+                    atomicAdd(&a_st[k], (unsigned long long)c << 32 | sum_tot);
                     atomicAdd(&a_wx[k], wx);
                     atomicAdd(&a_wy[k], wy);
                     atomicMin(&a_min[k], mn);
                     if (want_max) atomicMax(&a_max[k], mx);
                 } else {
                     Slot &sl = w.slot[r];
-                    atomicAdd(&sl.size, cnt);
+                    atomicAdd(&sl.size, c);
                     atomicAdd(&sl.tot, (unsigned long long)sum_tot);
                     atomicAdd(&sl.wx, wx);
                     atomicAdd(&sl.wy, wy);
