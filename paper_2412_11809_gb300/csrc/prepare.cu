@@ -48,6 +48,7 @@ __global__ void k_setup(Work w, int nsegs) {
         p.lsd_passes = 0;
         p.redo_count = 0;
         p.border_count = 0;
+        p.merge_count = 0;
         p.err = 0;
         p.ntiles = tile;
         if (tile > p.tile_cap || off > p.pos_cap) {

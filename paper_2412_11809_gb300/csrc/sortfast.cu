@@ -230,15 +230,15 @@ __global__ void __launch_bounds__(LS_THREADS, 3) k_tile_sort(Work w) {
 
 // Merge the second half of tile t-1 with the first half of tile t (both
 // sorted by (key, position)), in place.
+template <uint32_t CAP>
 struct LmShared {
-    uint32_t key[TILE];
-    uint32_t pos[TILE];
-    uint32_t pix[TILE];
-    uint16_t tot[TILE];
-    uint16_t rank[TILE];         // output rank of each moving element
+    uint32_t key[CAP];
+    uint32_t pos[CAP];
+    uint32_t pix[CAP];
+    uint16_t tot[CAP];
+    uint16_t rank[CAP];          // output rank of each moving element
     uint32_t cut[2];
 };
-constexpr int LM_SMEM = (int)sizeof(LmShared);
 
 // (key, position) of a below (key, position) of b
 __device__ __forceinline__ bool lm_below(uint32_t ka, uint32_t pa, uint32_t kb, uint32_t pb) {
@@ -257,13 +257,21 @@ __device__ __forceinline__ bool lm_below(uint32_t ka, uint32_t pa, uint32_t kb, 
 // elements' pixels and ToTs are staged in shared memory, so that the final
 // pass can write every array straight to its output position.
 constexpr uint32_t MERGE_BAND = TILE / 4;
+// k_tile_merge<false> stages two bands (a small CTA, many per SM) and lists
+// the borders whose overlap is wider than a band; k_tile_merge<true> takes
+// those with the whole window (TILE / 2 on each side).
+template <bool BIG>
+constexpr int lm_smem() { return (int)sizeof(LmShared<BIG ? (uint32_t)TILE : 2 * MERGE_BAND>); }
 
+template <bool BIG>
 __global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
     extern __shared__ __align__(16) unsigned char lm_raw[];
-    LmShared &S = *reinterpret_cast<LmShared *>(lm_raw);
+    LmShared<BIG ? (uint32_t)TILE : 2 * MERGE_BAND> &S =
+        *reinterpret_cast<LmShared<BIG ? (uint32_t)TILE : 2 * MERGE_BAND> *>(lm_raw);
     const Prob &P = *w.prob;
-    const uint32_t nt = P.ntiles;
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    const uint32_t nt = BIG ? P.merge_count : P.ntiles;   // the big kernel: the listed borders
+    for (uint32_t u = blockIdx.x; u < nt; u += gridDim.x) {
+        const uint32_t t = BIG ? w.redo[u] : u;
         const Seg &g = w.seg[w.tile_seg[t]];
         if (t == g.tile0) continue;
         uint32_t begin, end;
@@ -273,7 +281,8 @@ __global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
             const uint32_t ka = w.keys[0][begin - 1], kb = w.keys[0][begin];
             if (ka < kb || (ka == kb && w.vals[0][begin - 1] < w.vals[0][begin])) continue;
         }
-        for (uint32_t band = MERGE_BAND;; band = TILE / 2) {
+        {
+            const uint32_t band = BIG ? TILE / 2 : MERGE_BAND;
             const uint32_t na = band, nb = band < nb_all ? band : nb_all;
             const uint32_t a0 = begin - na;   // A = [a0, begin), B = [begin, begin + nb)
             if (threadIdx.x < 2) S.cut[threadIdx.x] = 0;
@@ -301,9 +310,10 @@ __global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
             __syncthreads();
             const uint32_t ia = S.cut[0], ib = S.cut[1];
             const bool contained = (ia > 0 || na == TILE / 2) && (ib < nb || nb == nb_all);
-            if (!contained && band != TILE / 2) {
+            if (!BIG && !contained) {   // overlap wider than the band: the whole window, later
+                if (threadIdx.x == 0) w.redo[atomicAdd(&w.prob->merge_count, 1u)] = t;
                 __syncthreads();
-                continue;   // overlap wider than the band: take the whole window
+                continue;
             }
             // moving part: A[ia, na) then B[0, ib) (indices in S); outputs a0 + ia ...
             const uint32_t ma = na - ia, m = ma + ib;
@@ -332,7 +342,6 @@ __global__ void __launch_bounds__(LS_THREADS) k_tile_merge(Work w) {
                 w.stot[o] = S.tot[src];
             }
             __syncthreads();
-            break;
         }
     }
 }
@@ -358,14 +367,20 @@ __global__ void __launch_bounds__(256) k_sort_check(Work w) {
 cudaError_t init_sortfast_attributes() {
     cudaError_t e = cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tile_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, LM_SMEM);
+    e = cudaFuncSetAttribute(k_tile_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lm_smem<false>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tile_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lm_smem<true>());
 }
 
 void launch_sort_fast(const Work &w, const Launch &L) {
     k_tile_sort<<<L.fit(k_tile_sort, LS_THREADS, LS_SMEM, G_SORT), LS_THREADS, LS_SMEM, L.stream>>>(w);
     L.mark("k_tile_sort");
-    k_tile_merge<<<L.fit(k_tile_merge, LS_THREADS, LM_SMEM, G_SORT), LS_THREADS, LM_SMEM, L.stream>>>(w);
+    k_tile_merge<false><<<L.fit(k_tile_merge<false>, LS_THREADS, lm_smem<false>(), G_SORT), LS_THREADS,
+                          lm_smem<false>(), L.stream>>>(w);
     L.mark("k_tile_merge");
+    k_tile_merge<true><<<L.fit(k_tile_merge<true>, LS_THREADS, lm_smem<true>(), G_SORT), LS_THREADS,
+                         lm_smem<true>(), L.stream>>>(w);
+    L.mark("k_tile_merge_big");
     k_sort_check<<<L.fit(k_sort_check, 256, 0), 256, 0, L.stream>>>(w);
     L.mark("k_sort_check");
 }

@@ -99,6 +99,7 @@ struct Prob {
     uint32_t lsd_passes;   // passes the radix sort needs (max over segments)
     uint32_t redo_count;   // tiles the table-mode link left to the general link kernel
     uint32_t border_count; // tile borders k_border_fast left to k_border_link
+    uint32_t merge_count;  // tile borders k_tile_merge left to its whole-window form (listed in redo)
 };
 
 // Feature sums of one cluster, kept at its root's sorted position.  One

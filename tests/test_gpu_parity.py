@@ -131,6 +131,20 @@ def test_input_permutation():
     check_against_oracle(hits[perm], 256, 256, 128)
 
 
+@pytest.mark.parametrize("window", [2400, 5000])
+def test_wide_disorder_merge_windows(window):
+    """Streams shuffled over wider windows than the bench stream's 1000
+    positions: at 2400 the sorted tiles of every border interleave over more
+    than the merge's first band (1024 positions on each side; about 1200
+    here), so the borders are merged over the whole window (2048 on each
+    side); at 5000 they interleave over about 2400 and the step takes the
+    general radix sort.
+    Both must give the oracle's clusters (t-ordered input, Section 3.1)."""
+    hits, _ = synth.generate(256, 256, 600_000, 40 + window, hit_rate_hz=40e6, track_frac=0.2,
+                             dead_time=True, shuffle_window=window)
+    check_against_oracle(hits, 256, 256, synth.DT_200NS)
+
+
 def test_empty_flush():
     with Clusterer(256, 256, 128) as c:
         c.flush()
