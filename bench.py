@@ -15,8 +15,10 @@ are independent; no collective on the data path); value = hits of all ranks
 / max-over-ranks time.  The reference arm (--impl reference) times the CPU
 oracle on the host cores over a bounded sample of the same stream.
 
-Besides value, the JSON line carries: roofline (dominant kernel) and
-kernel_roofline; kernel_ms (one profiled step); e2e (pinned host buffers in,
+Besides value, the JSON line carries: roofline (the whole path: hits/s x
+the algorithmic bytes per hit against the measured HBM copy rate, with the
+step's stored DRAM traffic), kernel_roofline and issue_roofline (the
+dominant kernel); kernel_ms (one profiled step); e2e (pinned host buffers in,
 host results out); cpu_baseline (the oracle, one core, a bounded sample);
 cpu_parallel (the paper's temporal-split CPU method on every host core, with
 its merge-cascade counters and thread scaling); clocks; and, unless
